@@ -1,0 +1,274 @@
+"""Benchmark: plain random walker on the 256^3 three-ellipsoid phantom.
+
+One step = one complete rw_solve (normalisation/quantisation, FP32 PCG with
+FP64 reductions, FP64-residual refinement to ||r|| <= 1e-8 ||b||) on inputs
+already resident in HBM.  Metric: voxel-CG-iterations/s = sum over the step of
+free voxels x PCG iterations, divided by the device time (CUDA events, max
+over ranks).  The 256^3 working set streamed per sweep (about 370 MB) is
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure, as it
+stands) on the host cores: each step is a bounded number of its PCG
+iterations on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-CG-iterations/s and HBM GB/s (% of peak) at <=1e-4 prob error vs FP64"
+UNIT = "voxel-iter/s"
+N = 256
+BETA = 130.0
+TOL = 1e-8
+SWEEP_BYTES_PER_VOXEL = 27   # x(delta) r+w 8, u r+w 8, p r+w 8, g 2, code 1  (FP32 vectors, unorm16 g)
+WORKLOAD = "plain random walker, 256^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(c, seconds=15.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample:
+    its first M PCG iterations on the same 256^3 system (M sized to ~seconds)."""
+    import oracle as O
+    q = O.quantize(c["volume"])
+    g = O.dequantize(q)
+    xin = np.where(c["code"] == 1, c["value"].astype(np.float64), 0.0)
+    nfree = int(np.count_nonzero(c["code"] == 0))
+    t0 = time.perf_counter()
+    O.rw_solve(g, c["code"], xin, BETA, tol=1e-13, max_iter=5)
+    t1 = time.perf_counter()
+    per = max((t1 - t0) / 6.0, 1e-3)           # ~ setup + 5 iterations
+    m = int(max(5, min(2000, seconds / per)))
+    t0 = time.perf_counter()
+    _, it, _, _ = O.rw_solve(g, c["code"], xin, BETA, tol=1e-13, max_iter=m)
+    dt = time.perf_counter() - t0
+    return {"value": nfree * it / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle Jacobi-PCG, first {it} iterations of the 256^3 system ({nfree} free voxels), "
+                      f"{dt:.1f} s incl. weight set-up"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import phantoms as P
+    import oracle as O
+    c = P.plain_ellipsoids(n=N, seed=0)
+    q = O.quantize(c["volume"])
+    g = O.dequantize(q)
+    xin = np.where(c["code"] == 1, c["value"].astype(np.float64), 0.0)
+    nfree = int(np.count_nonzero(c["code"] == 0))
+    iters_per_step = 20
+    for _ in range(args.warmup):
+        O.rw_solve(g, c["code"], xin, BETA, tol=1e-13, max_iter=2)
+    tot_it, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        _, it, _, _ = O.rw_solve(g, c["code"], xin, BETA, tol=1e-13, max_iter=iters_per_step)
+        tot_it += it
+    dt = time.perf_counter() - t0
+    v = nfree * tot_it / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "voxels": N ** 3, "free_voxels": nfree,
+                       "step": f"{iters_per_step} FP64 PCG iterations of the oracle (plus its weight set-up)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{iters_per_step} iterations per step x {args.steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import paper_2103_09564_gb300 as rw
+    import phantoms as P
+    c = P.plain_ellipsoids(n=N, seed=0)
+    vol = torch.from_numpy(c["volume"]).to(dev)
+    code = torch.from_numpy(c["code"]).to(dev)
+    val = torch.from_numpy(c["value"]).to(dev)
+    out = torch.empty_like(vol)
+    opts = rw.Opts(beta=BETA, tol=TOL)
+
+    def step():
+        _, st = rw.rw_solve(vol, code, val, opts, out=out)
+        return st
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    stats = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            stats.append(step())
+        e1.record()
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    vi = sum(s["voxel_iters"] for s in stats)
+    sweeps = sum(s["sweeps"] for s in stats)
+    ms_sweeps = sum(s["ms_sweeps"] for s in stats)
+    launches = sum(s["launches"] for s in stats)
+    if pg:
+        t = torch.tensor([ms, float(vi)], device=dev, dtype=torch.float64)
+        tm = t.clone()
+        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+        ts = t.clone()
+        pg.all_reduce(ts, op=pg.ReduceOp.SUM)
+        ms_all, vi_all = float(tm[0]), float(ts[1])
+    else:
+        ms_all, vi_all = ms, float(vi)
+    value = vi_all / (ms_all / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    vol_h = np.ascontiguousarray(c["volume"])
+    code_h = np.ascontiguousarray(c["code"])
+    val_h = np.ascontiguousarray(c["value"])
+    out_h = np.empty_like(vol_h)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vi_e2e = 0
+    for _ in range(e2e_steps):
+        _, st = rw.rw_solve(vol_h, code_h, val_h, opts, out=out_h)
+        vi_e2e += st["voxel_iters"]
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": vi_e2e / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(vol_h.nbytes + code_h.nbytes + val_h.nbytes),
+           "d2h_bytes_per_step": int(out_h.nbytes)}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+    peak, src = _peaks()
+    t_launch_s = (ms_sweeps / max(sweeps, 1)) / 1e3
+    alg = SWEEP_BYTES_PER_VOXEL * N ** 3
+    achieved = alg / t_launch_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "voxels": N ** 3, "free_voxels": int(stats[0]["free_voxels"]),
+                       "precision": "FP32 vectors/stencil, FP64 reductions + FP64-residual refinement",
+                       "tol": TOL, "iters_per_solve": stats[0]["iters"], "refine_rounds": stats[0]["refine_rounds"],
+                       "rel_resid": stats[0]["rel_resid"], "replicas": ws,
+                       "l2": "inputs larger than L2 (about 370 MB streamed per sweep), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_sweep (fused PCG sweep)", "peak_source": src,
+                         "algorithmic_bytes_per_launch": alg, "launch_ms": t_launch_s * 1e3,
+                         "sweeps_per_step": sweeps / args.steps},
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(c)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/* rw_api.h — C ABI of the GB300 hierarchical random walker library (librw.so).
+ *
+ * The method is the random walker of Sec. III-B of "Hierarchical Random Walker
+ * Segmentation for Large Volumetric Biomedical Images" (Drees, Eilers, Jiang,
+ * arXiv 2103.09564) and its hierarchical form H / H_p (Sec. IV, Eqs. 1-3).
+ *
+ * Conventions shared by every entry point
+ * - Arrays are dense, x fastest: element (x, y, z) of volume b is at
+ *   ((b * dims[2] + z) * dims[1] + y) * dims[0] + x.
+ * - Pointers may be device pointers (used in place) or host pointers (the
+ *   library copies them through its workspace); the kind is detected with
+ *   cudaPointerGetAttributes.  Caller-owned memory is never freed or kept.
+ * - Opaque handles (rw_pyramid, rw_tree) are owned by the library and freed
+ *   by the matching *_free call.
+ * - Every call runs on `stream` (a cudaStream_t, NULL = legacy default
+ *   stream) and synchronises it before returning, so outputs and rw_stats are
+ *   valid on return.  Device-side conditions (non-convergence) are reported
+ *   through the status of the same call.
+ * - Errors: a non-RW_OK status; rw_last_error() returns a thread-local text.
+ *   RW_ERR_NOT_CONVERGED still writes the best iterate.
+ * - The library keeps one internal device workspace (grown with cudaMalloc,
+ *   released by rw_release_workspace); calls are serialised by a mutex.
+ */
+#ifndef RW_API_H
+#define RW_API_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rw_status {
+    RW_OK = 0,
+    RW_ERR_INVALID_ARG = 1,    /* bad pointer, size, dtype or option */
+    RW_ERR_NO_SEEDS = 2,       /* a system without any seed has no unique solution */
+    RW_ERR_NOT_CONVERGED = 3,  /* max_iter reached before the tolerance */
+    RW_ERR_TIMEOUT = 4,        /* reserved: no kernel of this library waits on a flag */
+    RW_ERR_OOM = 5,            /* device allocation failed */
+    RW_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+    RW_ERR_UNIMPLEMENTED = 7
+} rw_status;
+
+typedef enum rw_dtype { RW_U16 = 0, RW_F32 = 1 } rw_dtype;
+
+/* How intensities are stored on the device after normalisation.
+ * UNORM16: q = round_half_even(g * 65535) (2 B/voxel, the default; weights
+ * then see g = q / 65535).  F32: g kept as FP32 (needed for gradients). */
+typedef enum rw_storage { RW_STORE_UNORM16 = 0, RW_STORE_F32 = 1 } rw_storage;
+
+/* RW_MIXED: FP32 vectors and stencil, FP64 reductions and FP64-residual
+ * iterative refinement.  RW_FP64: every vector and weight in FP64. */
+typedef enum rw_precision { RW_MIXED = 0, RW_FP64 = 1 } rw_precision;
+
+/* Seed codes of rw_seed_mask.code. */
+enum { RW_CODE_FREE = 0, RW_CODE_SEED = 1, RW_CODE_ABSENT = 2 };
+
+/* Node flags returned by rw_tree_node_stats (one int32 per brick). */
+enum {
+    RW_NODE_SOLVED = 1, RW_NODE_PRUNABLE = 2, RW_NODE_HOM = 4, RW_NODE_DT = 8,
+    RW_NODE_CFL = 16, RW_NODE_SIMILAR = 32, RW_NODE_REUSED = 64, RW_NODE_CFL_ADDED = 128,
+    RW_NODE_NO_SEEDS = 256
+};
+
+/* Intensity volume.  Normalisation (a reading: the paper applies
+ * w = exp(-beta (n[p]-n[q])^2) to intensities without fixing their scale):
+ *   normalize = 1: g = clamp((v - lo) / (hi - lo), 0, 1) in FP32;
+ *   normalize = 0: F32 input is used as g (clamped to [0, 1]), U16 input is
+ *   taken as unorm16. */
+typedef struct rw_volume {
+    const void* data;    /* [batch][z][y][x] */
+    int32_t dtype;       /* rw_dtype */
+    int32_t storage;     /* rw_storage */
+    int64_t dims[3];     /* x, y, z of one volume */
+    int64_t batch;       /* independent volumes, >= 1 (0 is read as 1) */
+    float lo, hi;        /* normalisation window */
+    int32_t normalize;
+    int32_t reserved;
+} rw_volume;
+
+/* Dense seeds for the plain solve, same shape as the volume.
+ * code: RW_CODE_FREE (unknown), RW_CODE_SEED (Dirichlet value from `value`),
+ * RW_CODE_ABSENT (not a vertex).  value: seed values in [0, 1]; it may be
+ * NULL when all seeds are background (0). */
+typedef struct rw_seed_mask {
+    const uint8_t* code;
+    const float* value;
+} rw_seed_mask;
+
+/* Label points (Sec. IV-A: labels are 3-D points with a value in [0, 1]).
+ * HOST memory.  xyz: n x 3 leaf-voxel coordinates (x, y, z); voxel i spans
+ * [i, i + 1).  At level k a label falls into voxel floor(q / 2^(K-k)). */
+typedef struct rw_labels {
+    const double* xyz;
+    const float* value;
+    int64_t n;
+} rw_labels;
+
+typedef struct rw_opts {
+    float beta;            /* Gaussian weight parameter (Sec. III-B), default 130 */
+    float w_min;           /* lower clamp of the weights, default 1e-30 */
+    double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2, default 1e-8 */
+    int32_t max_iter;      /* PCG iteration cap per system, default 20000 */
+    int32_t precision;     /* rw_precision, default RW_MIXED */
+    int32_t refine_rounds; /* FP64-residual refinement rounds (RW_MIXED), default 4 */
+    int32_t brick_size;    /* s (Sec. IV-A), default 32 */
+    float expand;          /* e (Sec. IV-B), default 1.25 */
+    float t_hom;           /* Sec. IV-D1, default 0.3 */
+    float t_bin;           /* Sec. IV-D1, default 0.01 */
+    float t_inc;           /* Sec. IV-E, default 0.01 */
+    int32_t prune_hom;     /* enable hom pruning, default 1 */
+    int32_t prune_dt;      /* enable dt pruning, default 1 */
+    int32_t iters_per_graph; /* PCG sweeps per captured CUDA graph (even), default 32 */
+    int32_t tile;          /* sweep tile: 0 = autotuned choice, else an RW_TILE_* value */
+    int32_t batch_bricks;  /* 1: one batched launch per level (default); 0: bricks one by one */
+    int32_t max_batch;     /* bricks per batched launch, default 8192 */
+} rw_opts;
+
+enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, RW_TILE_40x20 = 4,
+       RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7 };
+
+typedef struct rw_stats {
+    int32_t iters;          /* max PCG iterations over the systems of the call */
+    int32_t refine_rounds;  /* FP64-residual rounds run */
+    double rel_resid;       /* max over systems of the final FP64 ||b - A x|| / ||b|| */
+    int64_t voxel_iters;    /* sum over systems of free voxels x iterations */
+    int64_t free_voxels;    /* sum of free voxels */
+    int64_t bricks_active;  /* nodes processed by the call */
+    int64_t bricks_solved;
+    int64_t bricks_pruned;
+    int64_t bricks_reused;
+    int64_t bricks_conflict;
+    int64_t sweeps;         /* fused PCG sweep kernels launched */
+    double ms;              /* wall time of the call */
+    double ms_solve;        /* time inside the PCG loops */
+    double ms_sweeps;       /* device time of the fused sweeps (CUDA events on the library stream) */
+    int64_t launches;       /* kernels launched by the call */
+} rw_stats;
+
+typedef struct rw_pyramid rw_pyramid;
+typedef struct rw_tree rw_tree;
+
+void rw_opts_default(rw_opts* opts);
+const char* rw_last_error(void);
+const char* rw_version(void);
+/* Frees the internal workspace (cached device buffers). */
+rw_status rw_release_workspace(void);
+
+/* Plain random walker, Sec. III-B: for each of `vol->batch` volumes solve
+ *   L_U x_U = -B^T x_M   (Dirichlet problem, 6-connected graph,
+ *   w_pq = max(exp(-beta (g_p - g_q)^2), w_min))
+ * by matrix-free Jacobi-PCG.  x0: optional initial guess (NULL = 0) on free
+ * voxels, same layout as the volume.  x_out: full result (seeds carry their
+ * value, absent voxels 0), float32, same layout.  Returns RW_ERR_NO_SEEDS if
+ * a volume has no seed.  A volume whose right-hand side is 0 gets x_U = 0. */
+rw_status rw_solve(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opts* opts,
+                   const float* x0, float* x_out, rw_stats* stats, void* stream);
+
+/* Adjoint of rw_solve (not in the paper; gradient of a loss l(x)): solves
+ * L_U lambda = (dl/dx)_U with the same PCG (L_U is symmetric) and returns
+ *   dl/dg_i    = sum over edges e at i of dl/dw_e * dw_e/dg_i,
+ *   dl/dbeta   = sum over edges of dl/dw_e * dw_e/dbeta,
+ * with dl/dw_pq = -(lambda_p - lambda_q)(x_p - x_q) (lambda = 0 on seeds).
+ * x: the solution from rw_solve.  dloss_dg (nullable): float32 like the
+ * volume (gradient w.r.t. the normalised intensity g).  dloss_dbeta
+ * (nullable): `batch` doubles. */
+rw_status rw_solve_adjoint(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opts* opts,
+                           const float* x, const float* dloss_dx, float* dloss_dg,
+                           double* dloss_dbeta, rw_stats* stats, void* stream);
+
+/* LOD pyramid, Sec. III-A: leaf = normalised unorm16 volume; each coarser
+ * level is the 2x2x2 mean (existing children only at odd borders, Sec. IV-A)
+ * with ceil-halved dims, until every dim is <= brick_size (the root). */
+rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid** out, void* stream);
+/* Number of levels and their dims (levels x 3, x/y/z; level 0 = root). */
+rw_status rw_pyramid_info(const rw_pyramid* pyr, int32_t* n_levels, int64_t* dims);
+/* Copy level `level` (FP32 intensities; the leaf as q / 65535) to `out`. */
+rw_status rw_pyramid_read_level(const rw_pyramid* pyr, int32_t level, float* out, void* stream);
+void rw_pyramid_free(rw_pyramid* pyr);
+
+/* Output tree of H_p over `pyr` (kept alive by the caller until rw_tree_free). */
+rw_status rw_tree_create(const rw_pyramid* pyr, const rw_opts* opts, rw_tree** out);
+
+/* One level of the top-down procedure (Fig. 3).  level 0: root solve (Eq. 1)
+ * with `labels` (stored in the tree; NULL keeps the stored ones).  level k >= 1:
+ * all children of solved, non-prunable level-(k-1) nodes are solved in
+ * batched launches on their neighbourhood (Eq. 3, s_e = floor(e s)) with user
+ * seeds and continuous border seeds upsampled from level k-1 (Eq. 2), started
+ * from the upsampled parent (Sec. IV-D2); hom / dt / cfl / prunable are
+ * evaluated (Sec. IV-D1); absent nodes take the upsampled parent field.
+ * Levels must be refined in order 0, 1, ..., K. */
+rw_status rw_refine_level(rw_tree* tree, int32_t level, const rw_labels* labels, rw_stats* stats,
+                          void* stream);
+
+/* Incremental labelling, Sec. IV-E: add labels and update every level: the
+ * root is re-solved from the old root; children of re-solved nodes that are
+ * neither similar (max |new - old| < t_inc without conflicts involving added
+ * labels) nor prunable are re-solved from the old field; similar nodes keep
+ * their old values and whole old subtree.  Requires a fully refined tree. */
+rw_status rw_update_seeds(rw_tree* tree, const rw_labels* added, rw_stats* stats, void* stream);
+
+/* Copy box [x0,x1) x [y0,y1) x [z0,z1) (box = {x0,y0,z0,x1,y1,z1}) of the
+ * filled probability field of `level` to `out` (x fastest). */
+rw_status rw_tree_read_level(const rw_tree* tree, int32_t level, const int64_t box[6], float* out,
+                             void* stream);
+
+/* Per-node results of the last pass over `level` (host arrays of *n_nodes
+ * entries, brick order x fastest; pass NULL to query the count): RW_NODE_*
+ * flags, brick minimum, maximum and max |new - old| (incremental pass). */
+rw_status rw_tree_node_stats(const rw_tree* tree, int32_t level, int64_t* n_nodes, int32_t* flags,
+                             float* mn, float* mx, float* maxdiff);
+void rw_tree_free(rw_tree* tree);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RW_API_H */

@@ -1,0 +1,1293 @@
+// C ABI of librw.so (declared in include/rw_api.h): argument checks, the
+// device workspace, the PCG driver (refinement rounds, CUDA-graph chunks of
+// fused sweeps, per-system convergence), the adjoint, the LOD pyramid and the
+// hierarchical tree (Sec. IV, Fig. 3 processing scheme, level by level).
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "rw_api.h"
+#include "rw_internal.h"
+
+using namespace rwk;
+
+namespace {
+
+thread_local std::string g_err;
+std::recursive_mutex g_mu;
+int64_t g_launches = 0;   // kernels launched since the current call started (guarded by g_mu)
+
+// Count a kernel launch made through one of the rwk::launch_* helpers.
+inline cudaError_t counted(cudaError_t e) {
+    ++g_launches;
+    return e;
+}
+
+rw_status fail(rw_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                                 \
+    do {                                                                                                         \
+        cudaError_t e_ = (call);                                                                                 \
+        if (e_ != cudaSuccess) {                                                                                 \
+            cudaGetLastError();                                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? RW_ERR_OOM : RW_ERR_CUDA, "%s failed: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
+        }                                                                                                        \
+    } while (0)
+
+#define RCK(expr)                       \
+    do {                                \
+        rw_status r_ = (expr);          \
+        if (r_ != RW_OK) return r_;     \
+    } while (0)
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// Workspace: named slots of device memory, grown on demand and cached.
+enum Slot {
+    S_G, S_U0, S_U1, S_P0, S_P1, S_DELTA, S_XHI, S_PART, S_RPART, S_SC, S_NACT, S_VOL, S_CODE, S_VAL, S_X0, S_OUT,
+    S_RHS, S_EXT, S_JOBS, S_LAB, S_BFLAGS, S_STATS, S_POOL_G, S_POOL_CODE, S_POOL_X, S_ADJ_PART, S_DBETA, S_DG,
+    S_XF, S_STATUS, S_COUNT
+};
+
+struct DevWorkspace {
+    void* p[S_COUNT] = {};
+    size_t cap[S_COUNT] = {};
+    cudaStream_t stream = nullptr;
+    int* pinned = nullptr;
+    int sms = 0;
+};
+
+std::map<int, DevWorkspace> g_ws;
+
+rw_status ws_dev(DevWorkspace** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    DevWorkspace& w = g_ws[dev];
+    if (!w.stream) {
+        CK(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+        CK(cudaMallocHost(&w.pinned, 64));
+        CK(cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    *out = &w;
+    return RW_OK;
+}
+
+rw_status ws_get(DevWorkspace* w, int slot, size_t bytes, void** out) {
+    if (bytes == 0) bytes = 256;
+    if (w->cap[slot] < bytes) {
+        if (w->p[slot]) {
+            CK(cudaStreamSynchronize(w->stream));
+            CK(cudaFree(w->p[slot]));
+        }
+        w->p[slot] = nullptr;
+        w->cap[slot] = 0;
+        size_t nb = ((bytes + bytes / 8) + 4095) & ~(size_t)4095;
+        CK(cudaMalloc(&w->p[slot], nb));
+        w->cap[slot] = nb;
+    }
+    *out = w->p[slot];
+    return RW_OK;
+}
+
+template <typename P>
+rw_status ws_get_t(DevWorkspace* w, int slot, size_t bytes, P** out) {
+    void* v = nullptr;
+    RCK(ws_get(w, slot, bytes, &v));
+    *out = static_cast<P*>(v);
+    return RW_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself, or a staged copy.
+rw_status stage_in(DevWorkspace* w, int slot, const void* p, size_t bytes, const void** out) {
+    if (!p) {
+        *out = nullptr;
+        return RW_OK;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return RW_OK;
+    }
+    void* d = nullptr;
+    RCK(ws_get(w, slot, bytes, &d));
+    CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, w->stream));
+    *out = d;
+    return RW_OK;
+}
+
+// Caller stream -> internal stream ordering (inputs produced on `user` are complete).
+rw_status enter(DevWorkspace** w, void* user) {
+    RCK(ws_dev(w));
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(user)));
+    return RW_OK;
+}
+
+rw_status leave(DevWorkspace* w) {
+    CK(cudaStreamSynchronize(w->stream));
+    CK(cudaGetLastError());
+    return RW_OK;
+}
+
+rw_status check_opts(const rw_opts& o) {
+    if (!(o.beta >= 0.0f) || !(o.w_min >= 0.0f) || !(o.tol >= 0.0) || o.max_iter < 1 || o.refine_rounds < 0 ||
+        (o.precision != RW_MIXED && o.precision != RW_FP64) || o.iters_per_graph < 2 || o.tile < 0 || o.tile > 7 ||
+        o.brick_size < 2 || !(o.expand >= 1.0f) || o.max_batch < 1)
+        return fail(RW_ERR_INVALID_ARG, "invalid rw_opts");
+    return RW_OK;
+}
+
+rw_status check_volume(const rw_volume* v, int64_t* nvox, int64_t* batch) {
+    if (!v || !v->data) return fail(RW_ERR_INVALID_ARG, "volume or volume data is NULL");
+    if (v->dtype != RW_U16 && v->dtype != RW_F32) return fail(RW_ERR_INVALID_ARG, "unknown dtype %d", v->dtype);
+    if (v->storage != RW_STORE_UNORM16 && v->storage != RW_STORE_F32)
+        return fail(RW_ERR_INVALID_ARG, "unknown storage %d", v->storage);
+    for (int a = 0; a < 3; ++a)
+        if (v->dims[a] < 1 || v->dims[a] > (1 << 20)) return fail(RW_ERR_INVALID_ARG, "bad dims");
+    *batch = v->batch < 1 ? 1 : v->batch;
+    *nvox = v->dims[0] * v->dims[1] * v->dims[2];
+    if (*batch > 65535) return fail(RW_ERR_INVALID_ARG, "batch > 65535");
+    if (*nvox > ((int64_t)1 << 40)) return fail(RW_ERR_INVALID_ARG, "volume too large");
+    return RW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep configuration and the autotuner (tile shape, z-chunk, sweeps per graph).
+struct SweepCfg {
+    int tile = 1, tx = 32, ty = 16, nt = 512, zc = 64, ntx = 1, nty = 1, nzc = 1, grid = 1, ipg = 32;
+};
+
+std::map<std::string, std::pair<int, int>> g_tuned;  // class -> (tile, iters per graph)
+
+std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
+    std::vector<int> c;
+    if (fp64) {
+        c = {7, 3};
+    } else if (gtype == G_U16) {
+        c = {1, 2, 7};
+    } else if (nx <= 48) {
+        c = {3, 4, 7, 1};
+    } else if (nx <= 96 && nx % 80 == 0) {
+        c = {5, 6, 1, 2};
+    } else {
+        c = {1, 2, 7, 6};
+    }
+    std::vector<int> ok;
+    for (int t : c)
+        if (sweep_occupancy(fp64, gtype, t) > 0) ok.push_back(t);
+    return ok;
+}
+
+rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int ipg, SweepCfg* c) {
+    if (sweep_occupancy(fp64, gtype, tile) <= 0) {
+        return fail(RW_ERR_INVALID_ARG, "sweep tile %d not available for this precision/storage", tile);
+    }
+    CK(sweep_prepare(fp64, gtype, tile));
+    c->tile = tile;
+    tile_dims(tile, &c->tx, &c->ty);
+    c->nt = sweep_threads(tile);
+    c->ntx = (bx.nx + c->tx - 1) / c->tx;
+    c->nty = (bx.ny + c->ty - 1) / c->ty;
+    const int occ = std::max(1, sweep_occupancy(fp64, gtype, tile));
+    const int64_t want = (int64_t)2 * occ * sms;
+    const int64_t per_plane = (int64_t)bx.nbox * c->ntx * c->nty;
+    int nzc = (int)std::max<int64_t>(1, (want + per_plane - 1) / per_plane);
+    int zc = (bx.nz + nzc - 1) / nzc;
+    zc = std::max(zc, std::min(bx.nz, 16));
+    c->zc = zc;
+    c->nzc = (bx.nz + zc - 1) / zc;
+    const int64_t nwork = per_plane * c->nzc;
+    c->grid = (int)std::min<int64_t>(nwork, (int64_t)occ * sms);
+    c->ipg = ipg;
+    return RW_OK;
+}
+
+std::string class_key(int fp64, int gtype, const Boxes& bx) {
+    char b[160];
+    int nb = 1;
+    while (nb < bx.nbox) nb *= 4;
+    snprintf(b, sizeof(b), "%d/%d/%dx%dx%d/%d", fp64, gtype, bx.nx, bx.ny, bx.nz, nb);
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// The PCG driver.
+struct SolveProblem {
+    Boxes bx;
+    const void* g;
+    int gtype;
+    const uint8_t* code;
+    const float* value;
+    const float* x0;
+    const float* rhs;
+    double* x_hi;
+    int init_x;
+};
+
+struct SolveResult {
+    std::vector<BoxScalars> sc;
+    int rounds = 0;
+    int64_t sweeps = 0;
+    double ms_solve = 0.0;
+    double ms_sweeps = 0.0;   // device time of the graph-launched sweeps
+    int tile = 0;
+    int ipg = 0;
+};
+
+rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* const u[2], void* const p[2],
+                           int fp64, int gtype, int* n_active_dev, int64_t* sweeps, int64_t cap, double* ms_dev) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
+    int par = 0;
+    cudaError_t le = cudaSuccess;
+    for (int j = 0; j < cfg.ipg; ++j) {
+        sa.u_in = u[par];
+        sa.p_in = p[par];
+        sa.u_out = u[par ^ 1];
+        sa.p_out = p[par ^ 1];
+        cudaError_t e = launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream);
+        if (e != cudaSuccess && le == cudaSuccess) le = e;
+        par ^= 1;
+    }
+    cudaError_t ce = cudaStreamEndCapture(w->stream, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        CK(le);
+    }
+    CK(ce);
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    int n_act = 1;
+    rw_status st = RW_OK;
+    while (n_act > 0 && *sweeps < cap) {
+        cudaError_t e = cudaEventRecord(ev0, w->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, w->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev1, w->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w->pinned, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(RW_ERR_CUDA, "PCG chunk failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        *ms_dev += ms;
+        *sweeps += cfg.ipg;
+        g_launches += cfg.ipg;
+        n_act = *w->pinned;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaGraphExecDestroy(exec);
+    return st;
+}
+
+// Time `reps` sweeps of one tile on the live state (they are real PCG
+// iterations; an even count keeps the buffer parity).
+rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* const u[2], void* const p[2], int fp64,
+                    int gtype, int reps, float* ms) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, w->stream));
+    int par = 0;
+    for (int j = 0; j < reps; ++j) {
+        sa.u_in = u[par];
+        sa.p_in = p[par];
+        sa.u_out = u[par ^ 1];
+        sa.p_out = p[par ^ 1];
+        CK(counted(launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream)));
+        par ^= 1;
+    }
+    CK(cudaEventRecord(e1, w->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return RW_OK;
+}
+
+rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, SolveResult* R) {
+    const int fp64 = o.precision == RW_FP64 ? 1 : 0;
+    const Boxes& bx = P.bx;
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    const int64_t ntot = nvox * bx.nbox;
+    const size_t tsz = fp64 ? 8 : 4;
+    void *u[2], *p[2];
+    float* delta = nullptr;
+    BoxScalars* sc = nullptr;
+    int* nact = nullptr;
+    double *rpart = nullptr, *part = nullptr;
+    RCK(ws_get(w, S_U0, ntot * tsz, &u[0]));
+    RCK(ws_get(w, S_U1, ntot * tsz, &u[1]));
+    RCK(ws_get(w, S_P0, ntot * tsz, &p[0]));
+    RCK(ws_get(w, S_P1, ntot * tsz, &p[1]));
+    if (!fp64) RCK(ws_get_t(w, S_DELTA, ntot * 4, &delta));
+    RCK(ws_get_t(w, S_SC, bx.nbox * sizeof(BoxScalars), &sc));
+    RCK(ws_get_t(w, S_NACT, 64, &nact));
+    const int bpb = (int)((nvox + 255) / 256);
+    RCK(ws_get_t(w, S_RPART, (size_t)bx.nbox * bpb * 4 * sizeof(double), &rpart));
+
+    // configuration: cached autotuned choice, an explicit tile, or a default
+    const std::string key = class_key(fp64, P.gtype, bx);
+    std::vector<int> cands = tile_candidates(fp64, P.gtype, bx.nx);
+    if (cands.empty()) return fail(RW_ERR_INVALID_ARG, "no sweep kernel for this precision/storage");
+    int tile = cands[0];
+    int ipg = std::max(2, o.iters_per_graph & ~1);
+    bool tune = false;
+    if (o.tile != RW_TILE_AUTO) {
+        tile = o.tile;
+    } else {
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            tile = it->second.first;
+            ipg = it->second.second;
+        } else {
+            tune = true;
+        }
+    }
+    SweepCfg cfg;
+    RCK(make_cfg(fp64, P.gtype, tile, bx, w->sms, ipg, &cfg));
+    size_t part_elems = 0;
+    for (int t : cands) {
+        SweepCfg c2;
+        RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2));
+        part_elems = std::max(part_elems, (size_t)bx.nbox * c2.ntx * c2.nty * c2.nzc * 3);
+    }
+    {
+        size_t own = (size_t)bx.nbox * cfg.ntx * cfg.nty * cfg.nzc * 3;
+        part_elems = std::max(part_elems, own);
+    }
+    RCK(ws_get_t(w, S_PART, part_elems * sizeof(double), &part));
+
+    ResidArgs ra;
+    ra.bx = bx;
+    ra.g = P.g;
+    ra.gtype = P.gtype;
+    ra.code = P.code;
+    ra.value = P.value;
+    ra.x0 = P.x0;
+    ra.rhs = P.rhs;
+    ra.x = P.x_hi;
+    ra.u = u[0];
+    ra.p = p[0];
+    ra.part = rpart;
+    ra.blocks_per_box = bpb;
+    ra.mbeta = -(double)o.beta;
+    ra.wmin = (double)o.w_min;
+
+    CK(cudaMemsetAsync(sc, 0, bx.nbox * sizeof(BoxScalars), w->stream));
+    if (P.init_x) CK(counted(launch_init_x(fp64, ra, w->stream)));
+    CK(counted(launch_residual(fp64, ra, delta, w->stream)));
+    CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 1, w->stream)));
+    CK(counted(launch_zero_homog(fp64, bx, P.code, sc, P.x_hi, w->stream)));
+
+    SweepArgs sa;
+    sa.bx = bx;
+    sa.g = P.g;
+    sa.code = P.code;
+    sa.x = fp64 ? (void*)P.x_hi : (void*)delta;
+    sa.sc = sc;
+    sa.partials = part;
+    sa.n_active = nact;
+    sa.c2f = (float)(-(double)o.beta * 1.4426950408889634);
+    sa.wminf = o.w_min;
+    sa.mbeta = -(double)o.beta;
+    sa.wmin = (double)o.w_min;
+
+    const int rounds = fp64 ? 1 : std::max(1, o.refine_rounds);
+    const double eps_inner = fp64 ? 0.0 : 1e-5;
+    const double t0 = now_ms();
+    for (int r = 0; r < rounds; ++r) {
+        CK(cudaMemsetAsync(nact, 0, sizeof(int), w->stream));
+        CK(counted(launch_start_round(sc, bx.nbox, r, o.tol, eps_inner, o.max_iter, nact, w->stream)));
+        CK(cudaMemcpyAsync(w->pinned, nact, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+        if (*w->pinned == 0) break;
+        R->rounds = r + 1;
+        if (tune) {
+            // autotune on the first round of a new problem class: 4 sweeps per
+            // candidate tile, keep the fastest; sweeps per graph target ~1 ms
+            float best = 1e30f;
+            int best_tile = tile;
+            for (int t : cands) {
+                SweepCfg c2;
+                RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2));
+                SweepArgs s2 = sa;
+                s2.ntx = c2.ntx;
+                s2.nty = c2.nty;
+                s2.nzc = c2.nzc;
+                s2.zc = c2.zc;
+                float ms = 0;
+                RCK(time_tile(w, c2, s2, u, p, fp64, P.gtype, 4, &ms));
+                R->sweeps += 4;
+                if (ms < best) {
+                    best = ms;
+                    best_tile = t;
+                }
+            }
+            const float per = best / 4.0f;
+            int k = (int)std::lround(1.0 / std::max(per, 1e-4f));
+            k = std::max(8, std::min(64, k)) & ~1;
+            RCK(make_cfg(fp64, P.gtype, best_tile, bx, w->sms, k, &cfg));
+            g_tuned[key] = std::make_pair(best_tile, k);
+            tune = false;
+        }
+        sa.ntx = cfg.ntx;
+        sa.nty = cfg.nty;
+        sa.nzc = cfg.nzc;
+        sa.zc = cfg.zc;
+        const int64_t cap = R->sweeps + (int64_t)o.max_iter + 4 * cfg.ipg;
+        RCK(run_graph_chunks(w, cfg, sa, u, p, fp64, P.gtype, nact, &R->sweeps, cap, &R->ms_sweeps));
+        if (!fp64) CK(counted(launch_accumulate(ntot, P.code, delta, P.x_hi, w->stream)));
+        CK(counted(launch_residual(fp64, ra, delta, w->stream)));
+        CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
+    }
+    R->sc.resize(bx.nbox);
+    CK(cudaMemcpyAsync(R->sc.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    R->ms_solve = now_ms() - t0;
+    R->tile = cfg.tile;
+    R->ipg = cfg.ipg;
+    return RW_OK;
+}
+
+void stats_from(const SolveResult& R, const rw_opts& o, rw_stats* st, int* n_unconverged, int* n_noseed) {
+    int it = 0;
+    double rel = 0.0;
+    int64_t vi = 0, nf = 0;
+    int bad = 0, nos = 0;
+    for (const BoxScalars& S : R.sc) {
+        it = std::max(it, S.iters);
+        vi += (int64_t)S.iters * S.nfree;
+        nf += S.nfree;
+        if (S.nseed == 0) {
+            ++nos;
+            continue;
+        }
+        if (S.bb > 0.0) {
+            const double r = std::sqrt(S.rr_true / S.bb);
+            rel = std::max(rel, r);
+            if (r > o.tol) ++bad;
+        }
+    }
+    if (st) {
+        st->iters = std::max(st->iters, it);
+        st->refine_rounds = std::max(st->refine_rounds, R.rounds);
+        st->rel_resid = std::max(st->rel_resid, rel);
+        st->voxel_iters += vi;
+        st->free_voxels += nf;
+        st->sweeps += R.sweeps;
+        st->ms_solve += R.ms_solve;
+        st->ms_sweeps += R.ms_sweeps;
+    }
+    if (n_unconverged) *n_unconverged = bad;
+    if (n_noseed) *n_noseed = nos;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void rw_opts_default(rw_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->beta = 130.0f;
+    o->w_min = 1e-30f;
+    o->tol = 1e-8;
+    o->max_iter = 20000;
+    o->precision = RW_MIXED;
+    o->refine_rounds = 4;
+    o->brick_size = 32;
+    o->expand = 1.25f;
+    o->t_hom = 0.3f;
+    o->t_bin = 0.01f;
+    o->t_inc = 0.01f;
+    o->prune_hom = 1;
+    o->prune_dt = 1;
+    o->iters_per_graph = 32;
+    o->tile = RW_TILE_AUTO;
+    o->batch_bricks = 1;
+    o->max_batch = 8192;
+}
+
+const char* rw_last_error(void) { return g_err.c_str(); }
+
+const char* rw_version(void) { return "rw-gb300 0.1 (sm_103a)"; }
+
+rw_status rw_release_workspace(void) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    for (auto& kv : g_ws) {
+        DevWorkspace& w = kv.second;
+        if (w.stream) cudaStreamSynchronize(w.stream);
+        for (int s = 0; s < S_COUNT; ++s)
+            if (w.p[s]) cudaFree(w.p[s]);
+        if (w.pinned) cudaFreeHost(w.pinned);
+        if (w.stream) cudaStreamDestroy(w.stream);
+        w = DevWorkspace();
+    }
+    g_ws.clear();
+    return RW_OK;
+}
+
+rw_status rw_solve(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opts* opts_in, const float* x0,
+                   float* x_out, rw_stats* stats, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_launches = 0;
+    const double t_start = now_ms();
+    rw_opts o;
+    if (opts_in) o = *opts_in;
+    else rw_opts_default(&o);
+    RCK(check_opts(o));
+    int64_t nvox = 0, batch = 1;
+    RCK(check_volume(vol, &nvox, &batch));
+    if (!seeds || !seeds->code) return fail(RW_ERR_INVALID_ARG, "seed mask code is NULL");
+    if (!x_out) return fail(RW_ERR_INVALID_ARG, "x_out is NULL");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    const int64_t ntot = nvox * batch;
+    const size_t vbytes = ntot * (vol->dtype == RW_U16 ? 2 : 4);
+    const void *dvol, *dcode, *dval, *dx0;
+    RCK(stage_in(w, S_VOL, vol->data, vbytes, &dvol));
+    RCK(stage_in(w, S_CODE, seeds->code, ntot, &dcode));
+    RCK(stage_in(w, S_VAL, seeds->value, ntot * 4, &dval));
+    RCK(stage_in(w, S_X0, x0, ntot * 4, &dx0));
+    const int gtype = vol->storage == RW_STORE_F32 ? G_F32 : G_U16;
+    void* g = nullptr;
+    RCK(ws_get(w, S_G, ntot * (gtype == G_U16 ? 2 : 4), &g));
+    CK(counted(launch_quantize(dvol, vol->dtype, ntot, vol->lo, vol->hi, vol->normalize, vol->storage, g, w->stream)));
+    double* xhi = nullptr;
+    RCK(ws_get_t(w, S_XHI, ntot * 8, &xhi));
+
+    SolveProblem P;
+    P.bx.nbox = (int)batch;
+    P.bx.nx = (int)vol->dims[0];
+    P.bx.ny = (int)vol->dims[1];
+    P.bx.nz = (int)vol->dims[2];
+    P.bx.ext = nullptr;
+    P.g = g;
+    P.gtype = gtype;
+    P.code = static_cast<const uint8_t*>(dcode);
+    P.value = static_cast<const float*>(dval);
+    P.x0 = static_cast<const float*>(dx0);
+    P.rhs = nullptr;
+    P.x_hi = xhi;
+    P.init_x = 1;
+    SolveResult R;
+    RCK(solve_boxes(w, P, o, &R));
+    const bool out_dev = is_device_ptr(x_out);
+    float* dout = x_out;
+    if (!out_dev) RCK(ws_get_t(w, S_OUT, ntot * 4, &dout));
+    CK(counted(launch_copy_out(0, P.bx, xhi, dout, w->stream)));
+    if (!out_dev) CK(cudaMemcpyAsync(x_out, dout, ntot * 4, cudaMemcpyDeviceToHost, w->stream));
+    RCK(leave(w));
+    int bad = 0, nos = 0;
+    stats_from(R, o, stats, &bad, &nos);
+    if (stats) {
+        stats->ms = now_ms() - t_start;
+        stats->launches = g_launches;
+    }
+    if (nos > 0) return fail(RW_ERR_NO_SEEDS, "%d volume(s) without any seed", nos);
+    if (bad > 0) return fail(RW_ERR_NOT_CONVERGED, "%d system(s) above tol after %d rounds", bad, R.rounds);
+    return RW_OK;
+}
+
+rw_status rw_solve_adjoint(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opts* opts_in, const float* x,
+                           const float* dloss_dx, float* dloss_dg, double* dloss_dbeta, rw_stats* stats,
+                           void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_launches = 0;
+    const double t_start = now_ms();
+    rw_opts o;
+    if (opts_in) o = *opts_in;
+    else rw_opts_default(&o);
+    RCK(check_opts(o));
+    int64_t nvox = 0, batch = 1;
+    RCK(check_volume(vol, &nvox, &batch));
+    if (!seeds || !seeds->code || !x || !dloss_dx) return fail(RW_ERR_INVALID_ARG, "NULL argument");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    const int64_t ntot = nvox * batch;
+    const size_t vbytes = ntot * (vol->dtype == RW_U16 ? 2 : 4);
+    const void *dvol, *dcode, *dx, *ddl;
+    RCK(stage_in(w, S_VOL, vol->data, vbytes, &dvol));
+    RCK(stage_in(w, S_CODE, seeds->code, ntot, &dcode));
+    RCK(stage_in(w, S_XF, x, ntot * 4, &dx));
+    RCK(stage_in(w, S_RHS, dloss_dx, ntot * 4, &ddl));
+    const int gtype = vol->storage == RW_STORE_F32 ? G_F32 : G_U16;
+    void* g = nullptr;
+    RCK(ws_get(w, S_G, ntot * (gtype == G_U16 ? 2 : 4), &g));
+    CK(counted(launch_quantize(dvol, vol->dtype, ntot, vol->lo, vol->hi, vol->normalize, vol->storage, g, w->stream)));
+    double* lam = nullptr;
+    RCK(ws_get_t(w, S_XHI, ntot * 8, &lam));
+    SolveProblem P;
+    P.bx.nbox = (int)batch;
+    P.bx.nx = (int)vol->dims[0];
+    P.bx.ny = (int)vol->dims[1];
+    P.bx.nz = (int)vol->dims[2];
+    P.bx.ext = nullptr;
+    P.g = g;
+    P.gtype = gtype;
+    P.code = static_cast<const uint8_t*>(dcode);
+    P.value = nullptr;  // lambda = 0 on seeds
+    P.x0 = nullptr;
+    P.rhs = static_cast<const float*>(ddl);
+    P.x_hi = lam;
+    P.init_x = 1;
+    SolveResult R;
+    RCK(solve_boxes(w, P, o, &R));
+
+    const int bpb = (int)((nvox + 255) / 256);
+    double *apart = nullptr, *dbeta = nullptr;
+    RCK(ws_get_t(w, S_ADJ_PART, (size_t)batch * bpb * sizeof(double), &apart));
+    RCK(ws_get_t(w, S_DBETA, (size_t)batch * sizeof(double), &dbeta));
+    float* ddg = nullptr;
+    const bool dg_dev = dloss_dg && is_device_ptr(dloss_dg);
+    if (dloss_dg) {
+        if (dg_dev) ddg = dloss_dg;
+        else RCK(ws_get_t(w, S_DG, ntot * 4, &ddg));
+    }
+    AdjArgs aa;
+    aa.bx = P.bx;
+    aa.g = g;
+    aa.gtype = gtype;
+    aa.code = P.code;
+    aa.x = static_cast<const float*>(dx);
+    aa.lam = lam;
+    aa.dg = ddg;
+    aa.part = apart;
+    aa.blocks_per_box = bpb;
+    aa.beta = (double)o.beta;
+    aa.wmin = (double)o.w_min;
+    CK(counted(launch_adjoint(aa, w->stream)));
+    CK(counted(launch_adjoint_reduce(apart, bpb, (int)batch, dbeta, w->stream)));
+    if (dloss_dg && !dg_dev) CK(cudaMemcpyAsync(dloss_dg, ddg, ntot * 4, cudaMemcpyDeviceToHost, w->stream));
+    if (dloss_dbeta) {
+        CK(cudaMemcpyAsync(dloss_dbeta, dbeta, batch * sizeof(double),
+                           is_device_ptr(dloss_dbeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, w->stream));
+    }
+    RCK(leave(w));
+    int bad = 0, nos = 0;
+    stats_from(R, o, stats, &bad, &nos);
+    if (stats) {
+        stats->ms = now_ms() - t_start;
+        stats->launches = g_launches;
+    }
+    if (nos > 0) return fail(RW_ERR_NO_SEEDS, "%d volume(s) without any seed", nos);
+    if (bad > 0) return fail(RW_ERR_NOT_CONVERGED, "%d adjoint system(s) above tol", bad);
+    return RW_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// LOD pyramid and hierarchical tree.
+struct rw_pyramid {
+    int K = 0;                               // leaf level index
+    int s = 32;
+    std::vector<std::array<int, 3>> dims;    // level 0 (root) .. K (leaf), x/y/z
+    uint16_t* leaf = nullptr;                // unorm16 leaf
+    std::vector<float*> lv;                  // FP32 levels 0..K-1 (lv[K] = nullptr)
+    int device = 0;
+};
+
+namespace {
+
+struct TreeLevel {
+    int nbx = 1, nby = 1, nbz = 1;
+    int64_t nb = 1;
+    float* P = nullptr;      // filled field
+    float* Pold = nullptr;   // previous filled field (incremental pass)
+    std::vector<int32_t> flags;
+    std::vector<float> mn, mx, md;
+    std::vector<uint8_t> status;  // 0 absent, 1 solved (new values), 2 reused (old values)
+};
+
+}  // namespace
+
+struct rw_tree {
+    const rw_pyramid* pyr = nullptr;
+    rw_opts opts;
+    std::vector<TreeLevel> L;
+    std::vector<double> lab_xyz;
+    std::vector<float> lab_val;
+    std::vector<uint8_t> lab_added;
+    int refined = 0;         // levels of the current pass done
+    int update = 0;          // current pass is incremental
+    std::vector<std::array<int, 3>> resolve, reused;  // node lists for the next level
+};
+
+namespace {
+
+struct LabelKey {
+    float value;
+    int conflict;
+    int added;
+};
+
+void rasterize(const rw_tree* t, int k, std::vector<LabelVox>* out) {
+    const rw_pyramid* py = t->pyr;
+    const int K = py->K;
+    const double scale = std::ldexp(1.0, -(K - k));
+    const auto& d = py->dims[k];
+    std::unordered_map<int64_t, LabelKey> m;
+    std::vector<int64_t> order;
+    const size_t n = t->lab_val.size();
+    for (size_t i = 0; i < n; ++i) {
+        const double fx = std::floor(t->lab_xyz[3 * i] * scale), fy = std::floor(t->lab_xyz[3 * i + 1] * scale),
+                     fz = std::floor(t->lab_xyz[3 * i + 2] * scale);
+        if (!(fx >= 0 && fy >= 0 && fz >= 0 && fx < d[0] && fy < d[1] && fz < d[2])) continue;
+        const int64_t key = ((int64_t)fz * d[1] + (int64_t)fy) * d[0] + (int64_t)fx;
+        auto it = m.find(key);
+        if (it == m.end()) {
+            m[key] = LabelKey{t->lab_val[i], 0, t->lab_added[i] ? 1 : 0};
+            order.push_back(key);
+        } else {
+            if (it->second.value != t->lab_val[i]) it->second.conflict = 1;
+            if (t->lab_added[i]) it->second.added = 1;
+        }
+    }
+    out->clear();
+    for (int64_t key : order) {
+        const LabelKey& L = m[key];
+        LabelVox v;
+        v.x = (int)(key % d[0]);
+        v.y = (int)((key / d[0]) % d[1]);
+        v.z = (int)(key / ((int64_t)d[0] * d[1]));
+        v.value = L.value;
+        v.flags = L.conflict ? (1 | (L.added ? 2 : 0)) : 0;
+        out->push_back(v);
+    }
+}
+
+void children(const rw_tree* t, int k, const std::array<int, 3>& b, std::vector<std::array<int, 3>>* out) {
+    const TreeLevel& C = t->L[k + 1];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                std::array<int, 3> c = {2 * b[0] + dx, 2 * b[1] + dy, 2 * b[2] + dz};
+                if (c[0] < C.nbx && c[1] < C.nby && c[2] < C.nbz) out->push_back(c);
+            }
+}
+
+BrickJob make_job(const rw_tree* t, int k, const std::array<int, 3>& b) {
+    const int s = t->pyr->s;
+    const int se = (int)std::floor((double)t->opts.expand * s);
+    const int mlo = (se - s) / 2, mhi = se - s - mlo;
+    const auto& d = t->pyr->dims[k];
+    BrickJob J;
+    J.bx = b[0];
+    J.by = b[1];
+    J.bz = b[2];
+    int r0[3], r1[3];
+    for (int a = 0; a < 3; ++a) {
+        const int lo = b[a] * s;
+        r0[a] = std::max(lo - mlo, 0);
+        r1[a] = std::min(lo + s + mhi, d[a]);
+    }
+    J.rx0 = r0[0];
+    J.ry0 = r0[1];
+    J.rz0 = r0[2];
+    J.ex = r1[0] - r0[0];
+    J.ey = r1[1] - r0[1];
+    J.ez = r1[2] - r0[2];
+    J.faces = 0;
+    if (k > 0) {
+        for (int a = 0; a < 3; ++a) {
+            if (r0[a] > 0) J.faces |= 1 << (2 * a);
+            if (r1[a] < d[a]) J.faces |= 1 << (2 * a + 1);
+        }
+    }
+    J.pad = 0;
+    return J;
+}
+
+int64_t brick_index(const TreeLevel& L, const std::array<int, 3>& b) {
+    return ((int64_t)b[2] * L.nby + b[1]) * L.nbx + b[0];
+}
+
+// Solve every node in `jobs` at level k (batched launches), contract into the
+// level field and evaluate the node predicates.
+rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std::array<int, 3>>& nodes,
+                      const std::vector<LabelVox>& labs, LabelVox* dlab, rw_stats* st) {
+    const rw_pyramid* py = t->pyr;
+    TreeLevel& L = t->L[k];
+    const auto& d = py->dims[k];
+    const int s = py->s;
+    const int se = std::max(s, (int)std::floor((double)t->opts.expand * s));
+    // the root's neighbourhood is the whole root level (dims <= s)
+    const int E = (k == 0) ? std::max(d[0], std::max(d[1], d[2])) : se;
+    const int maxb = t->opts.batch_bricks ? t->opts.max_batch : 1;
+    rw_opts o = t->opts;
+    for (size_t off = 0; off < nodes.size(); off += maxb) {
+        const int nb = (int)std::min<size_t>(maxb, nodes.size() - off);
+        std::vector<BrickJob> jobs(nb);
+        std::vector<int> ext(3 * nb);
+        for (int i = 0; i < nb; ++i) {
+            jobs[i] = make_job(t, k, nodes[off + i]);
+            ext[3 * i] = jobs[i].ex;
+            ext[3 * i + 1] = jobs[i].ey;
+            ext[3 * i + 2] = jobs[i].ez;
+        }
+        BrickJob* djobs = nullptr;
+        int *dext = nullptr, *dflags = nullptr;
+        float *pg = nullptr, *dstats = nullptr;
+        uint8_t* pcode = nullptr;
+        double* px = nullptr;
+        const int64_t pv = (int64_t)E * E * E;
+        RCK(ws_get_t(w, S_JOBS, nb * sizeof(BrickJob), &djobs));
+        RCK(ws_get_t(w, S_EXT, nb * 3 * sizeof(int), &dext));
+        RCK(ws_get_t(w, S_BFLAGS, nb * sizeof(int), &dflags));
+        RCK(ws_get_t(w, S_STATS, nb * 3 * sizeof(float), &dstats));
+        RCK(ws_get_t(w, S_POOL_G, pv * nb * 4, &pg));
+        RCK(ws_get_t(w, S_POOL_CODE, pv * nb, &pcode));
+        RCK(ws_get_t(w, S_POOL_X, pv * nb * 8, &px));
+        CK(cudaMemcpyAsync(djobs, jobs.data(), nb * sizeof(BrickJob), cudaMemcpyHostToDevice, w->stream));
+        CK(cudaMemcpyAsync(dext, ext.data(), nb * 3 * sizeof(int), cudaMemcpyHostToDevice, w->stream));
+        CK(cudaMemsetAsync(dflags, 0, nb * sizeof(int), w->stream));
+        Boxes bx;
+        bx.nbox = nb;
+        bx.nx = bx.ny = bx.nz = E;
+        bx.ext = dext;
+        GatherArgs ga;
+        ga.bx = bx;
+        ga.jobs = djobs;
+        ga.gq = (k == py->K) ? py->leaf : nullptr;
+        ga.gf = (k == py->K) ? nullptr : py->lv[k];
+        ga.lx = d[0];
+        ga.ly = d[1];
+        ga.lz = d[2];
+        ga.parent = k > 0 ? t->L[k - 1].P : nullptr;
+        ga.px = k > 0 ? py->dims[k - 1][0] : 1;
+        ga.py = k > 0 ? py->dims[k - 1][1] : 1;
+        ga.pz = k > 0 ? py->dims[k - 1][2] : 1;
+        ga.init = t->update ? L.Pold : nullptr;
+        ga.g_out = pg;
+        ga.code_out = pcode;
+        ga.x_out = px;
+        CK(counted(launch_gather(ga, w->stream)));
+        CK(counted(launch_apply_labels(bx, djobs, dlab, (int)labs.size(), pcode, px, dflags, w->stream)));
+        SolveProblem P;
+        P.bx = bx;
+        P.g = pg;
+        P.gtype = G_F32;
+        P.code = pcode;
+        P.value = nullptr;
+        P.x0 = nullptr;
+        P.rhs = nullptr;
+        P.x_hi = px;
+        P.init_x = 0;
+        SolveResult R;
+        RCK(solve_boxes(w, P, o, &R));
+        int bad = 0, nos = 0;
+        stats_from(R, o, st, &bad, &nos);
+        ContractArgs ca;
+        ca.bx = bx;
+        ca.jobs = djobs;
+        ca.s = s;
+        ca.x = px;
+        ca.field = L.P;
+        ca.old = t->update ? L.Pold : nullptr;
+        ca.lx = d[0];
+        ca.ly = d[1];
+        ca.lz = d[2];
+        ca.stats = dstats;
+        CK(counted(launch_contract(ca, w->stream)));
+        std::vector<float> hst(3 * nb);
+        std::vector<int> hfl(nb);
+        CK(cudaMemcpyAsync(hst.data(), dstats, nb * 3 * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaMemcpyAsync(hfl.data(), dflags, nb * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+        for (int i = 0; i < nb; ++i) {
+            const int64_t bi = brick_index(L, nodes[off + i]);
+            const float mn = hst[3 * i], mx = hst[3 * i + 1], md = hst[3 * i + 2];
+            int f = RW_NODE_SOLVED | (hfl[i] & (RW_NODE_CFL | RW_NODE_CFL_ADDED));
+            if (R.sc[i].nseed == 0) f |= RW_NODE_NO_SEEDS;
+            // Sec. IV-D1: hom, dt, prunable = (hom or dt) and not cfl
+            const bool hom = (mx - mn) < t->opts.t_hom;
+            const bool dt = (mn - 0.5f > t->opts.t_bin) || (0.5f - mx > t->opts.t_bin);
+            if (hom) f |= RW_NODE_HOM;
+            if (dt) f |= RW_NODE_DT;
+            const bool cfl = (f & RW_NODE_CFL) != 0;
+            if (((hom && t->opts.prune_hom) || (dt && t->opts.prune_dt)) && !cfl) f |= RW_NODE_PRUNABLE;
+            // Sec. IV-E: similar = max |new - old| < t_inc and no conflict with added labels
+            if (t->update && md < t->opts.t_inc && !(f & RW_NODE_CFL_ADDED)) f |= RW_NODE_SIMILAR;
+            L.flags[bi] = f;
+            L.mn[bi] = mn;
+            L.mx[bi] = mx;
+            L.md[bi] = md;
+            if (st) {
+                st->bricks_solved += 1;
+                if (cfl) st->bricks_conflict += 1;
+            }
+        }
+    }
+    return RW_OK;
+}
+
+rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
+    const rw_pyramid* py = t->pyr;
+    TreeLevel& L = t->L[k];
+    const auto& d = py->dims[k];
+    std::vector<std::array<int, 3>> nodes, reuse;
+    if (k == 0) {
+        nodes.push_back({0, 0, 0});
+    } else {
+        nodes = t->resolve;
+        reuse = t->reused;
+    }
+    std::fill(L.flags.begin(), L.flags.end(), 0);
+    std::fill(L.mn.begin(), L.mn.end(), 0.0f);
+    std::fill(L.mx.begin(), L.mx.end(), 0.0f);
+    std::fill(L.md.begin(), L.md.end(), 0.0f);
+    std::fill(L.status.begin(), L.status.end(), 0);
+    std::vector<LabelVox> labs;
+    rasterize(t, k, &labs);
+    LabelVox* dlab = nullptr;
+    RCK(ws_get_t(w, S_LAB, std::max<size_t>(1, labs.size()) * sizeof(LabelVox), &dlab));
+    if (!labs.empty())
+        CK(cudaMemcpyAsync(dlab, labs.data(), labs.size() * sizeof(LabelVox), cudaMemcpyHostToDevice, w->stream));
+    if (st) st->bricks_active += (int64_t)nodes.size();
+    RCK(solve_nodes(w, t, k, nodes, labs, dlab, st));
+    std::vector<std::array<int, 3>> nres, nreu;
+    for (const auto& b : nodes) {
+        const int64_t bi = brick_index(L, b);
+        const int f = L.flags[bi];
+        const bool similar = (f & RW_NODE_SIMILAR) != 0;
+        if (similar) {
+            L.status[bi] = 2;
+            if (k < py->K) children(t, k, b, &nreu);
+            if (st) st->bricks_reused += 1;
+        } else {
+            L.status[bi] = 1;
+            if (f & RW_NODE_PRUNABLE) {
+                if (st) st->bricks_pruned += 1;
+            } else if (k < py->K) {
+                children(t, k, b, &nres);
+            }
+        }
+    }
+    for (const auto& b : reuse) {
+        const int64_t bi = brick_index(L, b);
+        L.status[bi] = 2;
+        L.flags[bi] = RW_NODE_REUSED;
+        if (k < py->K) children(t, k, b, &nreu);
+        if (st) st->bricks_reused += 1;
+    }
+    uint8_t* dstatus = nullptr;
+    RCK(ws_get_t(w, S_STATUS, L.nb, &dstatus));
+    CK(cudaMemcpyAsync(dstatus, L.status.data(), L.nb, cudaMemcpyHostToDevice, w->stream));
+    FillArgs fa;
+    fa.field = L.P;
+    fa.lx = d[0];
+    fa.ly = d[1];
+    fa.lz = d[2];
+    fa.parent = k > 0 ? t->L[k - 1].P : nullptr;
+    fa.px = k > 0 ? py->dims[k - 1][0] : 1;
+    fa.py = k > 0 ? py->dims[k - 1][1] : 1;
+    fa.pz = k > 0 ? py->dims[k - 1][2] : 1;
+    fa.old = L.Pold;
+    fa.status = dstatus;
+    fa.nbx = L.nbx;
+    fa.nby = L.nby;
+    fa.nbz = L.nbz;
+    fa.s = py->s;
+    CK(counted(launch_fill(fa, w->stream)));
+    CK(cudaStreamSynchronize(w->stream));
+    t->resolve = nres;
+    t->reused = nreu;
+    std::sort(t->resolve.begin(), t->resolve.end());
+    t->resolve.erase(std::unique(t->resolve.begin(), t->resolve.end()), t->resolve.end());
+    std::sort(t->reused.begin(), t->reused.end());
+    t->reused.erase(std::unique(t->reused.begin(), t->reused.end()), t->reused.end());
+    return RW_OK;
+}
+
+rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
+    if (!lab || lab->n <= 0) return RW_OK;
+    if (!lab->xyz || !lab->value) return fail(RW_ERR_INVALID_ARG, "labels with NULL arrays");
+    if (is_device_ptr(lab->xyz) || is_device_ptr(lab->value))
+        return fail(RW_ERR_INVALID_ARG, "labels must be in host memory");
+    for (int64_t i = 0; i < lab->n; ++i) {
+        t->lab_xyz.push_back(lab->xyz[3 * i]);
+        t->lab_xyz.push_back(lab->xyz[3 * i + 1]);
+        t->lab_xyz.push_back(lab->xyz[3 * i + 2]);
+        t->lab_val.push_back(lab->value[i]);
+        t->lab_added.push_back((uint8_t)added);
+    }
+    return RW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid** out, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!out) return fail(RW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int64_t nvox = 0, batch = 1;
+    RCK(check_volume(vol, &nvox, &batch));
+    if (batch != 1) return fail(RW_ERR_INVALID_ARG, "a pyramid is built from one volume");
+    if (brick_size < 2) return fail(RW_ERR_INVALID_ARG, "brick_size < 2");
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    rw_pyramid* py = new rw_pyramid();
+    py->s = brick_size;
+    std::vector<std::array<int, 3>> dims;
+    std::array<int, 3> dd = {(int)vol->dims[0], (int)vol->dims[1], (int)vol->dims[2]};
+    dims.push_back(dd);
+    while (std::max(dd[0], std::max(dd[1], dd[2])) > brick_size) {
+        for (int a = 0; a < 3; ++a) dd[a] = (dd[a] + 1) / 2;
+        dims.push_back(dd);
+    }
+    std::reverse(dims.begin(), dims.end());
+    py->dims = dims;
+    py->K = (int)dims.size() - 1;
+    py->lv.assign(dims.size(), nullptr);
+    auto cleanup = [&](rw_status st) {
+        rw_pyramid_free(py);
+        return st;
+    };
+    cudaError_t e = cudaMalloc(&py->leaf, nvox * 2);
+    if (e != cudaSuccess) return cleanup(fail(RW_ERR_OOM, "pyramid leaf: %s", cudaGetErrorString(e)));
+    for (int k = 0; k < py->K; ++k) {
+        const int64_t n = (int64_t)dims[k][0] * dims[k][1] * dims[k][2];
+        e = cudaMalloc(&py->lv[k], n * 4);
+        if (e != cudaSuccess) return cleanup(fail(RW_ERR_OOM, "pyramid level %d: %s", k, cudaGetErrorString(e)));
+    }
+    const void* dvol = nullptr;
+    rw_status st = stage_in(w, S_VOL, vol->data, nvox * (vol->dtype == RW_U16 ? 2 : 4), &dvol);
+    if (st != RW_OK) return cleanup(st);
+    e = launch_quantize(dvol, vol->dtype, nvox, vol->lo, vol->hi, vol->normalize, RW_STORE_UNORM16, py->leaf,
+                        w->stream);
+    for (int k = py->K - 1; k >= 0 && e == cudaSuccess; --k) {
+        const auto& f = dims[k + 1];
+        if (k == py->K - 1) e = launch_downsample_u16(py->leaf, f[0], f[1], f[2], py->lv[k], w->stream);
+        else e = launch_downsample_f32(py->lv[k + 1], f[0], f[1], f[2], py->lv[k], w->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return cleanup(fail(RW_ERR_CUDA, "pyramid build: %s", cudaGetErrorString(e)));
+    cudaGetDevice(&py->device);
+    *out = py;
+    return RW_OK;
+}
+
+rw_status rw_pyramid_info(const rw_pyramid* py, int32_t* n_levels, int64_t* dims) {
+    if (!py) return fail(RW_ERR_INVALID_ARG, "pyramid is NULL");
+    if (n_levels) *n_levels = py->K + 1;
+    if (dims)
+        for (int k = 0; k <= py->K; ++k)
+            for (int a = 0; a < 3; ++a) dims[3 * k + a] = py->dims[k][a];
+    return RW_OK;
+}
+
+rw_status rw_pyramid_read_level(const rw_pyramid* py, int32_t level, float* out, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!py || !out || level < 0 || level > py->K) return fail(RW_ERR_INVALID_ARG, "bad pyramid level");
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    const auto& d = py->dims[level];
+    const int64_t n = (int64_t)d[0] * d[1] * d[2];
+    const bool dev = is_device_ptr(out);
+    float* dst = out;
+    if (!dev) RCK(ws_get_t(w, S_OUT, n * 4, &dst));
+    if (level == py->K) CK(counted(launch_leaf_to_f32(py->leaf, n, dst, w->stream)));
+    else CK(cudaMemcpyAsync(dst, py->lv[level], n * 4, cudaMemcpyDeviceToDevice, w->stream));
+    if (!dev) CK(cudaMemcpyAsync(out, dst, n * 4, cudaMemcpyDeviceToHost, w->stream));
+    return leave(w);
+}
+
+void rw_pyramid_free(rw_pyramid* py) {
+    if (!py) return;
+    if (py->leaf) cudaFree(py->leaf);
+    for (float* p : py->lv)
+        if (p) cudaFree(p);
+    delete py;
+}
+
+rw_status rw_tree_create(const rw_pyramid* py, const rw_opts* opts_in, rw_tree** out) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!py || !out) return fail(RW_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    rw_opts o;
+    if (opts_in) o = *opts_in;
+    else rw_opts_default(&o);
+    RCK(check_opts(o));
+    if (o.brick_size != py->s) return fail(RW_ERR_INVALID_ARG, "opts.brick_size != pyramid brick size");
+    rw_tree* t = new rw_tree();
+    t->pyr = py;
+    t->opts = o;
+    t->L.resize(py->K + 1);
+    for (int k = 0; k <= py->K; ++k) {
+        TreeLevel& L = t->L[k];
+        const auto& d = py->dims[k];
+        L.nbx = (d[0] + py->s - 1) / py->s;
+        L.nby = (d[1] + py->s - 1) / py->s;
+        L.nbz = (d[2] + py->s - 1) / py->s;
+        L.nb = (int64_t)L.nbx * L.nby * L.nbz;
+        const int64_t n = (int64_t)d[0] * d[1] * d[2];
+        cudaError_t e = cudaMalloc(&L.P, n * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&L.Pold, n * 4);
+        if (e == cudaSuccess) e = cudaMemset(L.P, 0, n * 4);
+        if (e == cudaSuccess) e = cudaMemset(L.Pold, 0, n * 4);
+        if (e != cudaSuccess) {
+            rw_tree_free(t);
+            return fail(RW_ERR_OOM, "tree level %d: %s", k, cudaGetErrorString(e));
+        }
+        L.flags.assign(L.nb, 0);
+        L.mn.assign(L.nb, 0.0f);
+        L.mx.assign(L.nb, 0.0f);
+        L.md.assign(L.nb, 0.0f);
+        L.status.assign(L.nb, 0);
+    }
+    *out = t;
+    return RW_OK;
+}
+
+rw_status rw_refine_level(rw_tree* t, int32_t level, const rw_labels* labels, rw_stats* stats, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_launches = 0;
+    const double t0 = now_ms();
+    if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
+    if (level < 0 || level > t->pyr->K) return fail(RW_ERR_INVALID_ARG, "level %d out of range", level);
+    if (level != 0 && level != t->refined) return fail(RW_ERR_INVALID_ARG, "levels must be refined in order");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (level == 0) {
+        if (labels) {
+            t->lab_xyz.clear();
+            t->lab_val.clear();
+            t->lab_added.clear();
+            RCK(copy_labels(t, labels, 0));
+        }
+        t->update = 0;
+        t->refined = 0;
+        t->resolve.clear();
+        t->reused.clear();
+    }
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    RCK(process_level(t, level, stats, w));
+    t->refined = level + 1;
+    RCK(leave(w));
+    if (stats) {
+        stats->ms = now_ms() - t0;
+        stats->launches = g_launches;
+    }
+    return RW_OK;
+}
+
+rw_status rw_update_seeds(rw_tree* t, const rw_labels* added, rw_stats* stats, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_launches = 0;
+    const double t0 = now_ms();
+    if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
+    if (t->refined != t->pyr->K + 1) return fail(RW_ERR_INVALID_ARG, "tree is not fully refined");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    for (auto& a : t->lab_added) a = 0;
+    RCK(copy_labels(t, added, 1));
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    for (auto& L : t->L) std::swap(L.P, L.Pold);
+    t->update = 1;
+    t->resolve.clear();
+    t->reused.clear();
+    t->refined = 0;
+    for (int k = 0; k <= t->pyr->K; ++k) {
+        rw_status st = process_level(t, k, stats, w);
+        if (st != RW_OK) return st;
+        t->refined = k + 1;
+    }
+    t->update = 0;
+    for (auto& a : t->lab_added) a = 0;
+    RCK(leave(w));
+    if (stats) {
+        stats->ms = now_ms() - t0;
+        stats->launches = g_launches;
+    }
+    return RW_OK;
+}
+
+rw_status rw_tree_read_level(const rw_tree* t, int32_t level, const int64_t box[6], float* out, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!t || !out || level < 0 || level > t->pyr->K) return fail(RW_ERR_INVALID_ARG, "bad arguments");
+    const auto& d = t->pyr->dims[level];
+    int64_t bb[6] = {0, 0, 0, d[0], d[1], d[2]};
+    if (box)
+        for (int i = 0; i < 6; ++i) bb[i] = box[i];
+    for (int a = 0; a < 3; ++a)
+        if (bb[a] < 0 || bb[a + 3] > d[a] || bb[a] > bb[a + 3]) return fail(RW_ERR_INVALID_ARG, "box outside level");
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    const int64_t n = (bb[3] - bb[0]) * (bb[4] - bb[1]) * (bb[5] - bb[2]);
+    const bool dev = is_device_ptr(out);
+    float* dst = out;
+    if (!dev) RCK(ws_get_t(w, S_OUT, n * 4, &dst));
+    CK(counted(launch_read_box(t->L[level].P, d[0], d[1], d[2], bb, dst, w->stream)));
+    if (!dev) CK(cudaMemcpyAsync(out, dst, n * 4, cudaMemcpyDeviceToHost, w->stream));
+    return leave(w);
+}
+
+rw_status rw_tree_node_stats(const rw_tree* t, int32_t level, int64_t* n_nodes, int32_t* flags, float* mn, float* mx,
+                             float* maxdiff) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!t || level < 0 || level > t->pyr->K) return fail(RW_ERR_INVALID_ARG, "bad arguments");
+    const TreeLevel& L = t->L[level];
+    if (n_nodes) *n_nodes = L.nb;
+    if (flags) memcpy(flags, L.flags.data(), L.nb * sizeof(int32_t));
+    if (mn) memcpy(mn, L.mn.data(), L.nb * sizeof(float));
+    if (mx) memcpy(mx, L.mx.data(), L.nb * sizeof(float));
+    if (maxdiff) memcpy(maxdiff, L.md.data(), L.nb * sizeof(float));
+    return RW_OK;
+}
+
+void rw_tree_free(rw_tree* t) {
+    if (!t) return;
+    for (auto& L : t->L) {
+        if (L.P) cudaFree(L.P);
+        if (L.Pold) cudaFree(L.Pold);
+    }
+    delete t;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Internal declarations shared by the CUDA translation units of librw.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rwk {
+
+enum : uint8_t { FREE = 0, SEED = 1, ABSENT = 2 };
+
+// Per-system PCG state that lives on the device (one per box).
+struct BoxScalars {
+    double gam;      // gamma_k = (r_k, u_k) of the last sweep
+    double alpha;    // alpha for the next sweep
+    double beta;     // beta for the next sweep
+    double rr;       // ||r||^2 (recursive)
+    double bb;       // ||b||^2
+    double tol2;     // the round stops when rr <= tol2
+    double rr_true;  // FP64 ||b - A x||^2 of the last residual sweep
+    double dbeta;    // adjoint: dl/dbeta
+    int iters;       // regular sweeps completed (all rounds)
+    int max_iter;
+    int active;      // 1 while the box iterates
+    int phase;       // 0: next sweep is the initial (alpha = beta = 0) sweep
+    int nseed;
+    int nfree;
+    unsigned counter;  // arrival counter of the last-block reduction
+    int status;      // 0 ok, 3 not converged, 2 no seeds
+};
+
+// A batch of equally padded boxes: box b covers [0,nx) x [0,ny) x [0,nz) in
+// its own storage; voxels at or beyond ext[b] are absent.
+struct Boxes {
+    int nbox;
+    int nx, ny, nz;
+    const int* ext;  // device [nbox][3] (x, y, z) or nullptr = full box
+};
+
+struct SweepArgs {
+    Boxes bx;
+    int ntx, nty, nzc, zc;  // tiles per box: x, y, z-chunks; chunk depth
+    const void* g;          // intensities (uint16 unorm or float)
+    const uint8_t* code;
+    void* x;                // iterate (T)
+    const void* u_in;       // u_k   (T)
+    const void* p_in;       // p_k-1 (T)
+    void* u_out;            // u_k+1 (T)
+    void* p_out;            // p_k   (T)
+    BoxScalars* sc;
+    double* partials;       // [nbox][tiles][3]
+    int* n_active;
+    float c2f;              // -beta * log2(e), FP32 weights
+    float wminf;
+    double mbeta;           // -beta, FP64 weights
+    double wmin;
+};
+
+enum GType { G_U16 = 0, G_F32 = 1 };
+enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE_80x8 = 5, TILE_80x16 = 6,
+              TILE_32x8 = 7 };
+
+// Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
+// combination that is not instantiated.
+cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s);
+size_t sweep_smem_bytes(int fp64, int tile);
+void tile_dims(int tile, int* tx, int* ty);
+int sweep_threads(int tile);
+cudaError_t sweep_prepare(int fp64, int gtype, int tile);  // opt-in dynamic smem
+int sweep_occupancy(int fp64, int gtype, int tile);         // resident CTAs per SM (0: not instantiated)
+
+// Residual / initial guess (solve_kernels.cu).
+struct ResidArgs {
+    Boxes bx;
+    const void* g;
+    int gtype;
+    const uint8_t* code;
+    const float* value;    // seed values (nullable)
+    const float* x0;       // initial guess (nullable)
+    const float* rhs;      // extra right-hand side on free voxels (nullable)
+    void* x;               // FP64 solution x_hi
+    void* u;               // out: u_0 = r / d  (T)
+    void* p;               // out: zeroed       (T)
+    double* part;          // [nbox][blocks][4]: bb, rr, nseed, nfree
+    int blocks_per_box;
+    double mbeta, wmin;
+};
+cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s);
+// fp64 = 0: also clears the FP32 correction vector `delta`.
+cudaError_t launch_residual(int fp64, const ResidArgs& a, float* delta, cudaStream_t s);
+cudaError_t launch_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x, cudaStream_t s);
+cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, BoxScalars* sc, int first,
+                              cudaStream_t s);
+cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
+                               int* n_active, cudaStream_t s);
+cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, const BoxScalars* sc, void* x,
+                              cudaStream_t s);
+cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s);
+
+// Normalisation / quantisation (hier_kernels.cu).
+cudaError_t launch_quantize(const void* v, int dtype, int64_t n, float lo, float hi, int normalize, int storage,
+                            void* out, cudaStream_t s);
+
+// Adjoint (adjoint_kernels.cu).
+struct AdjArgs {
+    Boxes bx;
+    const void* g;
+    int gtype;
+    const uint8_t* code;
+    const float* x;      // forward solution
+    const double* lam;   // adjoint solution (FP64)
+    float* dg;           // nullable
+    double* part;        // [nbox][blocks] dbeta partials
+    int blocks_per_box;
+    double beta, wmin;
+};
+cudaError_t launch_adjoint(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_reduce(const double* part, int blocks_per_box, int nbox, double* dbeta, cudaStream_t s);
+
+// Hierarchy (hier_kernels.cu).
+cudaError_t launch_downsample_u16(const uint16_t* fine, int nx, int ny, int nz, float* coarse, cudaStream_t s);
+cudaError_t launch_downsample_f32(const float* fine, int nx, int ny, int nz, float* coarse, cudaStream_t s);
+cudaError_t launch_leaf_to_f32(const uint16_t* q, int64_t n, float* out, cudaStream_t s);
+
+struct BrickJob {      // one active node of level k
+    int bx, by, bz;    // brick index
+    int rx0, ry0, rz0; // clipped neighbourhood origin (level voxels)
+    int ex, ey, ez;    // clipped neighbourhood extent
+    int faces;         // bit f set: face f (x0,x1,y0,y1,z0,z1) lies inside the level volume -> border seeds
+    int pad;
+};
+struct LabelVox {      // a rasterised label voxel at level k
+    int x, y, z;
+    float value;
+    int flags;         // 1: conflict, 2: conflict involves an added label
+};
+struct GatherArgs {
+    Boxes bx;                  // pool boxes (E^3 padded)
+    const BrickJob* jobs;
+    const float* gf;           // level intensities (FP32) or nullptr when gq used
+    const uint16_t* gq;        // leaf unorm16 (leaf level) or nullptr
+    int lx, ly, lz;            // level dims
+    const float* parent;       // filled level k-1 (nullptr at the root)
+    int px, py, pz;            // parent dims
+    const float* init;         // initial guess field at level k (nullptr: use the upsample / 0)
+    float* g_out;              // pool intensities (FP32)
+    uint8_t* code_out;
+    double* x_out;             // pool FP64 iterate
+};
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_apply_labels(const Boxes& bx, const BrickJob* jobs, const LabelVox* lab, int nlab,
+                                uint8_t* code, double* x, int* box_flags, cudaStream_t s);
+struct ContractArgs {
+    Boxes bx;
+    const BrickJob* jobs;
+    int s;                 // brick size
+    const double* x;       // pool solution (FP64)
+    float* field;          // level k field (written on the brick box)
+    const float* old;      // old level k field (nullable) for max |new - old|
+    int lx, ly, lz;
+    float* stats;          // [nbox][3]: min, max, maxdiff
+};
+cudaError_t launch_contract(const ContractArgs& a, cudaStream_t s);
+struct FillArgs {
+    float* field;
+    int lx, ly, lz;
+    const float* parent;    // level k-1 filled field (nullptr at root)
+    int px, py, pz;
+    const float* old;       // old level-k field (for reused nodes)
+    const uint8_t* status;  // per brick: 0 absent (upsample), 1 solved (keep), 2 reused (copy old)
+    int nbx, nby, nbz, s;
+};
+cudaError_t launch_fill(const FillArgs& a, cudaStream_t s);
+cudaError_t launch_read_box(const float* field, int lx, int ly, int lz, const int64_t box[6], float* out,
+                            cudaStream_t s);
+
+}  // namespace rwk

@@ -1,0 +1,320 @@
+// Set-up, residual and bookkeeping kernels of the PCG solve (Sec. III-B
+// system, Jacobi-PCG as in Sec. V), plus the sweep dispatcher.
+//
+// Precision scheme (mixed): the solution is held in FP64 (x_hi).  Each
+// refinement round computes the true residual r = b - A x_hi with FP64 edge
+// weights, starts the FP32 PCG on the correction system A delta = r
+// (delta = 0, u = D^-1 r, p = 0), and adds delta to x_hi when the round
+// ends.  In RW_FP64 mode the sweeps iterate on x_hi directly.
+#include "rw_internal.h"
+#include "sweep_kernel.cuh"
+
+namespace rwk {
+
+cudaError_t sweep_launch_f32_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep_launch_f32_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep_launch_d64_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep_launch_d64_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep_prepare_f32_u16(int tile);
+cudaError_t sweep_prepare_f32_f32(int tile);
+cudaError_t sweep_prepare_d64_u16(int tile);
+cudaError_t sweep_prepare_d64_f32(int tile);
+int sweep_occupancy_f32_u16(int tile);
+int sweep_occupancy_f32_f32(int tile);
+int sweep_occupancy_d64_u16(int tile);
+int sweep_occupancy_d64_f32(int tile);
+
+cudaError_t sweep_prepare(int fp64, int gtype, int tile);
+
+// Resident CTAs per SM of an instantiated sweep (0 when the combination is
+// not compiled); opts the kernel in to its dynamic shared memory first.
+int sweep_occupancy(int fp64, int gtype, int tile) {
+    static int cache[2][2][8];
+    static bool init = false;
+    if (!init) {
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 8; ++c) cache[a][b][c] = -1;
+        init = true;
+    }
+    if (tile < 1 || tile > 7) return 0;
+    int& slot = cache[fp64 ? 1 : 0][gtype == G_U16 ? 0 : 1][tile];
+    if (slot >= 0) return slot;
+    if (sweep_prepare(fp64, gtype, tile) != cudaSuccess) {
+        cudaGetLastError();
+        slot = 0;
+        return 0;
+    }
+    if (fp64) slot = gtype == G_U16 ? sweep_occupancy_d64_u16(tile) : sweep_occupancy_d64_f32(tile);
+    else slot = gtype == G_U16 ? sweep_occupancy_f32_u16(tile) : sweep_occupancy_f32_f32(tile);
+    return slot;
+}
+
+void tile_dims(int tile, int* tx, int* ty) {
+    static const int T[8][2] = {{0, 0}, {32, 16}, {64, 8}, {40, 8}, {40, 20}, {80, 8}, {80, 16}, {32, 8}};
+    if (tile < 1 || tile > 7) tile = 1;
+    *tx = T[tile][0];
+    *ty = T[tile][1];
+}
+
+int sweep_threads(int tile) {
+    static const int N[8] = {0, 512, 512, 320, 800, 640, 640, 256};
+    return (tile >= 1 && tile <= 7) ? N[tile] : 0;
+}
+
+size_t sweep_smem_bytes(int fp64, int tile) {
+    int tx, ty;
+    tile_dims(tile, &tx, &ty);
+    const int r2 = (tx + 4) * (ty + 4);
+    return fp64 ? (size_t)sweep_planes_bytes<double>(r2) : (size_t)sweep_planes_bytes<float>(r2);
+}
+
+cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s) {
+    if (fp64) return gtype == G_U16 ? sweep_launch_d64_u16(tile, a, grid, s) : sweep_launch_d64_f32(tile, a, grid, s);
+    return gtype == G_U16 ? sweep_launch_f32_u16(tile, a, grid, s) : sweep_launch_f32_f32(tile, a, grid, s);
+}
+
+cudaError_t sweep_prepare(int fp64, int gtype, int tile) {
+    if (fp64) return gtype == G_U16 ? sweep_prepare_d64_u16(tile) : sweep_prepare_d64_f32(tile);
+    return gtype == G_U16 ? sweep_prepare_f32_u16(tile) : sweep_prepare_f32_f32(tile);
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double gdbl(const void* g, int gtype, int64_t i) {
+    return gtype == G_U16 ? (double)static_cast<const uint16_t*>(g)[i] / 65535.0
+                          : (double)static_cast<const float*>(g)[i];
+}
+
+__device__ __forceinline__ bool box_extent(const Boxes& bx, int box, int* ex, int* ey, int* ez) {
+    if (bx.ext) {
+        *ex = bx.ext[3 * box];
+        *ey = bx.ext[3 * box + 1];
+        *ez = bx.ext[3 * box + 2];
+    } else {
+        *ex = bx.nx;
+        *ey = bx.ny;
+        *ez = bx.nz;
+    }
+    return true;
+}
+
+// x_hi: seeds take their value, free voxels the initial guess, others 0.
+__global__ void k_init_x(const ResidArgs a) {
+    const int box = blockIdx.y;
+    const int64_t nvox = (int64_t)a.bx.nx * a.bx.ny * a.bx.nz;
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nvox) return;
+    int ex, ey, ez;
+    box_extent(a.bx, box, &ex, &ey, &ez);
+    const int x = (int)(li % a.bx.nx), y = (int)((li / a.bx.nx) % a.bx.ny), z = (int)(li / ((int64_t)a.bx.nx * a.bx.ny));
+    const int64_t i = (int64_t)box * nvox + li;
+    double v = 0.0;
+    if (x < ex && y < ey && z < ez) {
+        const uint8_t c = a.code[i];
+        if (c == SEED) v = a.value ? (double)a.value[i] : 0.0;
+        else if (c == FREE) v = a.x0 ? (double)a.x0[i] : 0.0;
+    }
+    static_cast<double*>(a.x)[i] = v;
+}
+
+// FP64 residual r = b - A x_hi = rhs - sum_j w_ij (x_i - x_j) on free voxels
+// (x_j = seed value on seeds), with b = rhs + sum over seeded neighbours of
+// w_ij m_j.  Writes u = r / d (T), p = 0 and, in mixed mode, delta = 0; per
+// block partial sums of ||b||^2, ||r||^2, #seeds, #free.
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delta) {
+    const int box = blockIdx.y;
+    const int nx = a.bx.nx, ny = a.bx.ny, nz = a.bx.nz;
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    const int64_t li = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double bb = 0, rr = 0, ns = 0, nf = 0;
+    if (li < nvox) {
+        int ex, ey, ez;
+        box_extent(a.bx, box, &ex, &ey, &ez);
+        const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+        const int64_t base = (int64_t)box * nvox;
+        const int64_t i = base + li;
+        const double* xh = static_cast<const double*>(a.x);
+        T uo = 0;
+        if (x < ex && y < ey && z < ez) {
+            const uint8_t c = a.code[i];
+            if (c == SEED) ns = 1;
+            if (c == FREE) {
+                nf = 1;
+                const double gi = gdbl(a.g, a.gtype, i), xi = xh[i];
+                const double rh = a.rhs ? (double)a.rhs[i] : 0.0;
+                double d = 0, s = 0, b = rh;
+                const int nbx[6] = {x - 1, x + 1, x, x, x, x};
+                const int nby[6] = {y, y, y - 1, y + 1, y, y};
+                const int nbz[6] = {z, z, z, z, z - 1, z + 1};
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    if (nbx[k] < 0 || nbx[k] >= ex || nby[k] < 0 || nby[k] >= ey || nbz[k] < 0 || nbz[k] >= ez) continue;
+                    const int64_t j = base + ((int64_t)nbz[k] * ny + nby[k]) * nx + nbx[k];
+                    const uint8_t cj = a.code[j];
+                    if (cj == ABSENT) continue;
+                    const double dg = gi - gdbl(a.g, a.gtype, j);
+                    const double w = fmax(exp(a.mbeta * dg * dg), a.wmin);
+                    const double xj = xh[j];
+                    d += w;
+                    s += w * (xi - xj);
+                    if (cj == SEED) b += w * xj;
+                }
+                const double r = rh - s;
+                bb = b * b;
+                rr = r * r;
+                uo = d > 0.0 ? (T)(r / d) : (T)0;
+            }
+        }
+        static_cast<T*>(a.u)[i] = uo;
+        static_cast<T*>(a.p)[i] = (T)0;
+        if (delta) delta[i] = 0.0f;
+    }
+    __shared__ double red[4][8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bb += __shfl_down_sync(0xffffffffu, bb, o);
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        ns += __shfl_down_sync(0xffffffffu, ns, o);
+        nf += __shfl_down_sync(0xffffffffu, nf, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = bb;
+        red[1][wid] = rr;
+        red[2][wid] = ns;
+        red[3][wid] = nf;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0;
+        for (int k = 0; k < 8; ++k) s += red[threadIdx.x][k];
+        a.part[((int64_t)box * a.blocks_per_box + blockIdx.x) * 4 + threadIdx.x] = s;
+    }
+}
+
+cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s) {
+    (void)fp64;
+    const int64_t nvox = (int64_t)a.bx.nx * a.bx.ny * a.bx.nz;
+    dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)a.bx.nbox);
+    k_init_x<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(int fp64, const ResidArgs& a, float* delta, cudaStream_t s) {
+    dim3 grid((unsigned)a.blocks_per_box, (unsigned)a.bx.nbox);
+    if (fp64) k_residual<double><<<grid, 256, 0, s>>>(a, nullptr);
+    else k_residual<float><<<grid, 256, 0, s>>>(a, delta);
+    return cudaGetLastError();
+}
+
+__global__ void k_box_reduce(const double* part, int bpb, BoxScalars* sc, int first) {
+    __shared__ double red[4][256];
+    const int box = blockIdx.x;
+    double v[4] = {0, 0, 0, 0};
+    for (int k = threadIdx.x; k < bpb; k += 256)
+        for (int j = 0; j < 4; ++j) v[j] += part[((int64_t)box * bpb + k) * 4 + j];
+    for (int j = 0; j < 4; ++j) red[j][threadIdx.x] = v[j];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int j = 0; j < 4; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        BoxScalars* S = sc + box;
+        if (first) {
+            S->bb = red[0][0];
+            S->nseed = (int)red[2][0];
+            S->nfree = (int)red[3][0];
+        }
+        S->rr_true = red[1][0];
+    }
+}
+
+cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, BoxScalars* sc, int first,
+                              cudaStream_t s) {
+    k_box_reduce<<<nbox, 256, 0, s>>>(part, blocks_per_box, sc, first);
+    return cudaGetLastError();
+}
+
+// Decide which systems iterate in this round and set their inner target:
+// stop the round at ||r|| <= max(tol ||b||, eps_inner ||r_round_start||).
+__global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
+                              int* n_active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    BoxScalars* S = sc + b;
+    if (round == 0) {
+        S->iters = 0;
+        S->max_iter = max_iter;
+        S->status = 0;
+        S->dbeta = 0.0;
+    }
+    if (!(S->bb > 0.0)) S->rr_true = 0.0;
+    const double tgt = tol * tol * S->bb;
+    const bool need = S->nseed > 0 && S->nfree > 0 && S->bb > 0.0 && S->rr_true > tgt && S->iters < max_iter;
+    S->counter = 0u;
+    if (need) {
+        S->active = 1;
+        S->phase = 0;
+        S->alpha = 0.0;
+        S->beta = 0.0;
+        S->tol2 = fmax(tgt, eps_inner * eps_inner * S->rr_true);
+        atomicAdd(n_active, 1);
+    } else {
+        S->active = 0;
+    }
+}
+
+cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
+                               int* n_active, cudaStream_t s) {
+    k_start_round<<<(nbox + 127) / 128, 128, 0, s>>>(sc, nbox, round, tol, eps_inner, max_iter, n_active);
+    return cudaGetLastError();
+}
+
+// A system whose right-hand side is zero has x_U = 0.
+__global__ void k_zero_homog(const Boxes bx, const uint8_t* code, const BoxScalars* sc, double* x) {
+    const int box = blockIdx.y;
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nvox) return;
+    const BoxScalars* S = sc + box;
+    if (!(S->bb == 0.0) || S->nseed == 0) return;
+    const int64_t i = (int64_t)box * nvox + li;
+    if (code[i] == FREE) x[i] = 0.0;
+}
+
+cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, const BoxScalars* sc, void* x,
+                              cudaStream_t s) {
+    (void)fp64;
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)bx.nbox);
+    k_zero_homog<<<grid, 256, 0, s>>>(bx, code, sc, static_cast<double*>(x));
+    return cudaGetLastError();
+}
+
+// x_hi += delta on free voxels (end of a mixed-precision round).
+__global__ void k_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && code[i] == FREE) x[i] += (double)delta[i];
+}
+
+cudaError_t launch_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x, cudaStream_t s) {
+    k_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, code, delta, x);
+    return cudaGetLastError();
+}
+
+__global__ void k_copy_out(int64_t n, const double* x, float* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)x[i];
+}
+
+cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s) {
+    (void)fp64;
+    const int64_t n = (int64_t)bx.nbox * bx.nx * bx.ny * bx.nz;
+    k_copy_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, static_cast<const double*>(x), out);
+    return cudaGetLastError();
+}
+
+}  // namespace rwk

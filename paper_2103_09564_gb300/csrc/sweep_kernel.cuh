@@ -1,0 +1,330 @@
+// Fused PCG sweep: one kernel per iteration of the random walker solve
+// L_U x_U = -B^T x_M (Sec. III-B) with the Jacobi preconditioner (Sec. V,
+// CG with Jacobi preconditioner).
+//
+// The CG recurrences are arranged so that the two inner products of an
+// iteration are taken in the same sweep (the single-reduction arrangement of
+// Chronopoulos and Gear).  Storing u = D^-1 r instead of r, one sweep reads
+// x, u_k, p_k-1, g and the seed code and writes x, u_k+1 and p_k:
+//
+//   p_k    = u_k + beta_k p_k-1                    (pointwise, tile + halo 2)
+//   s_k    = A p_k                                  (7-point stencil, halo 1)
+//   x_k+1  = x_k + alpha_k p_k
+//   u_k+1  = u_k - alpha_k D^-1 s_k                 (halo 1)
+//   w_k+1  = A u_k+1                                (interior)
+//   gamma  = (r, u) = sum d u^2,  delta = (u, w),  rr = sum (d u)^2
+//
+// and alpha_k+1 = gamma_k+1 / (delta_k+1 - beta_k+1 gamma_k+1 / alpha_k),
+// beta_k+1 = gamma_k+1 / gamma_k are formed by the last CTA of the system.
+// A = D - W is never stored: the six edge weights
+// w = max(exp(-beta (g_p - g_q)^2), w_min) are recomputed from g in shared
+// memory (FP32: ex2.approx; FP64: exp).  Seeds keep u = p = 0, absent voxels
+// and voxels outside the box have no edges.
+//
+// Tiling: a CTA owns a TX x TY column block of one box and marches through a
+// z-chunk with ring buffers of planes (p and u_k with a 2-voxel halo, u_k+1
+// with a 1-voxel halo, forward edge weights), so every voxel of x, u, p is
+// read and written once per sweep from HBM; halo planes and columns come from
+// L2.  Per-thread partial sums run in T (at most one element per plane),
+// block and grid reductions in FP64 (warp shuffles, then the last CTA of the
+// system sums the per-CTA partials in a fixed order: results are
+// deterministic).  No CTA waits on another: the last-block pattern uses one
+// atomic counter per system and never spins.
+#pragma once
+
+#include "rw_internal.h"
+
+namespace rwk {
+
+__device__ __forceinline__ float ex2_approx(float a) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+    typedef float acc;
+    __device__ __forceinline__ static float w(float a, float b, const SweepArgs& A) {
+        const float d = a - b;
+        return fmaxf(ex2_approx(A.c2f * d * d), A.wminf);
+    }
+};
+template <>
+struct Num<double> {
+    typedef double acc;
+    __device__ __forceinline__ static double w(double a, double b, const SweepArgs& A) {
+        const double d = a - b;
+        return fmax(exp(A.mbeta * d * d), A.wmin);
+    }
+};
+
+template <typename T, typename G>
+__device__ __forceinline__ T gval(const G* g, int64_t i) {
+    if constexpr (sizeof(G) == 2) {
+        if constexpr (sizeof(T) == 4) return (float)g[i] * (1.0f / 65535.0f);
+        else return (double)g[i] / 65535.0;
+    } else {
+        return (T)g[i];
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void block_reduce3(double& a, double& b, double& c, double* red) {
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[wid] = a;
+        red[NW + wid] = b;
+        red[2 * NW + wid] = c;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < NW ? red[lane] : 0.0;
+        b = lane < NW ? red[NW + lane] : 0.0;
+        c = lane < NW ? red[2 * NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+    }
+    __syncthreads();
+}
+
+// Scalar recurrences of the system after its sweep (run by one thread of the
+// last CTA).  g = gamma_k+1, rr = ||r_k+1||^2, dl = delta_k+1.
+__device__ __forceinline__ void finalize_box(BoxScalars* S, double g, double rr, double dl, int* n_active) {
+    bool stop;
+    if (S->phase == 0) {
+        // initial sweep (alpha = beta = 0): gamma_0, delta_0
+        S->phase = 1;
+        S->rr = rr;
+        S->gam = g;
+        stop = !(rr > S->tol2) || !(g > 0.0) || !(dl > 0.0);
+        S->alpha = stop ? 0.0 : g / dl;
+        S->beta = 0.0;
+    } else {
+        S->iters += 1;
+        S->rr = rr;
+        const double bcg = g / S->gam;
+        const double den = dl - bcg * g / S->alpha;
+        stop = !(rr > S->tol2) || S->iters >= S->max_iter || !(g > 0.0) || !(den > 0.0);
+        if (!stop) {
+            S->beta = bcg;
+            S->alpha = g / den;
+            S->gam = g;
+        }
+    }
+    if (stop) {
+        S->active = 0;
+        atomicSub(n_active, 1);
+    }
+}
+
+template <typename T>
+constexpr int sweep_planes_bytes(int R2) {
+    return (int)sizeof(T) * R2 * 22 + 2 * R2;
+}
+
+template <typename T, typename G, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
+    constexpr int W2 = TX + 4, H2 = TY + 4, R2 = W2 * H2;
+    constexpr int W1 = TX + 2, H1 = TY + 2, R1 = W1 * H1;
+    typedef typename Num<T>::acc acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sP = reinterpret_cast<T*>(smem_raw);  // [3][R2] p_k
+    T* sUk = sP + 3 * R2;                     // [2][R2] u_k
+    T* sUn = sUk + 2 * R2;                    // [3][R2] u_k+1
+    T* sG = sUn + 3 * R2;                     // [2][R2] g
+    T* sWx = sG + 2 * R2;                     // [4][R2] weight (i, i+x)
+    T* sWy = sWx + 4 * R2;                    // [4][R2] weight (i, i+y)
+    T* sWz = sWy + 4 * R2;                    // [4][R2] weight (i-z, i)
+    uint8_t* sC = reinterpret_cast<uint8_t*>(sWz + 4 * R2);  // [2][R2] code
+    __shared__ double red[3 * (NT / 32)];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    const int tpb = A.ntx * A.nty * A.nzc;
+    const int64_t nwork = (int64_t)A.bx.nbox * tpb;
+    const int nx = A.bx.nx, ny = A.bx.ny, nz = A.bx.nz;
+    const int64_t bstride = (int64_t)nx * ny * nz;
+    const G* __restrict__ gin = static_cast<const G*>(A.g);
+    const uint8_t* __restrict__ cin = A.code;
+    T* __restrict__ X = static_cast<T*>(A.x);
+    const T* __restrict__ Uin = static_cast<const T*>(A.u_in);
+    const T* __restrict__ Pin = static_cast<const T*>(A.p_in);
+    T* __restrict__ Uout = static_cast<T*>(A.u_out);
+    T* __restrict__ Pout = static_cast<T*>(A.p_out);
+
+    for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int box = (int)(w / tpb);
+        const int t = (int)(w - (int64_t)box * tpb);
+        BoxScalars* S = A.sc + box;
+        if (!S->active) continue;  // same value for every thread of the CTA
+        const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
+        const T alpha = (T)S->alpha, bcg = (T)S->beta;
+        int ex = nx, ey = ny, ez = nz;
+        if (A.bx.ext) {
+            ex = A.bx.ext[3 * box];
+            ey = A.bx.ext[3 * box + 1];
+            ez = A.bx.ext[3 * box + 2];
+        }
+        const int ox = tx * TX, oy = ty * TY, z0 = tz * A.zc;
+        const int z1 = min(z0 + A.zc, ez);
+        const int64_t base = (int64_t)box * bstride;
+        acc a_gam = 0, a_rr = 0, a_del = 0;
+
+        if (ox < ex && oy < ey && z0 < ez) {
+            for (int zf = z0 - 2; zf <= z1 + 1; ++zf) {
+                const int f3 = (zf + 6) % 3, f2 = (zf + 6) & 1, f4 = (zf + 8) & 3, p2 = (zf + 5) & 1;
+                // -- A1: load plane zf (halo 2), p_k = u_k + beta p_k-1
+                for (int e = tid; e < R2; e += NT) {
+                    const int ix = e % W2, iy = e / W2;
+                    const int gx = ox + ix - 2, gy = oy + iy - 2;
+                    uint8_t c = ABSENT;
+                    T gv = 0, uk = 0, pm = 0;
+                    if (gx >= 0 && gx < ex && gy >= 0 && gy < ey && zf >= 0 && zf < ez) {
+                        const int64_t i = base + ((int64_t)zf * ny + gy) * nx + gx;
+                        c = cin[i];
+                        gv = gval<T, G>(gin, i);
+                        uk = Uin[i];
+                        pm = Pin[i];
+                    }
+                    sC[f2 * R2 + e] = c;
+                    sG[f2 * R2 + e] = gv;
+                    sUk[f2 * R2 + e] = uk;
+                    sP[f3 * R2 + e] = (c == FREE) ? uk + bcg * pm : (T)0;
+                }
+                __syncthreads();
+                // -- A2: forward edge weights of plane zf (and z-edges to zf-1)
+                for (int e = tid; e < R2; e += NT) {
+                    const int ix = e % W2, iy = e / W2;
+                    const uint8_t c0 = sC[f2 * R2 + e];
+                    const T g0 = sG[f2 * R2 + e];
+                    T wx = 0, wy = 0, wz = 0;
+                    if (c0 != ABSENT) {
+                        if (ix + 1 < W2 && sC[f2 * R2 + e + 1] != ABSENT) wx = Num<T>::w(g0, sG[f2 * R2 + e + 1], A);
+                        if (iy + 1 < H2 && sC[f2 * R2 + e + W2] != ABSENT) wy = Num<T>::w(g0, sG[f2 * R2 + e + W2], A);
+                        if (zf > z0 - 2 && sC[p2 * R2 + e] != ABSENT) wz = Num<T>::w(sG[p2 * R2 + e], g0, A);
+                    }
+                    sWx[f4 * R2 + e] = wx;
+                    sWy[f4 * R2 + e] = wy;
+                    sWz[f4 * R2 + e] = wz;
+                }
+                __syncthreads();
+                // -- B: plane zm = zf-1 on the halo-1 region
+                const int zm = zf - 1;
+                if (zm >= z0 - 1) {
+                    const int m3 = (zm + 6) % 3, m2 = (zm + 6) & 1, m4 = (zm + 8) & 3;
+                    const int l3 = (zm + 5) % 3;  // plane zm-1
+                    const T* P = sP + m3 * R2;
+                    const T* Pl = sP + l3 * R2;
+                    const T* Ph = sP + f3 * R2;
+                    const T* Wx = sWx + m4 * R2;
+                    const T* Wy = sWy + m4 * R2;
+                    const T* Wzl = sWz + m4 * R2;
+                    const T* Wzh = sWz + f4 * R2;
+                    const bool zint = (zm >= z0 && zm < z1);
+                    for (int e1 = tid; e1 < R1; e1 += NT) {
+                        const int jx = e1 % W1 + 1, jy = e1 / W1 + 1;
+                        const int e = jy * W2 + jx;
+                        const uint8_t c = sC[m2 * R2 + e];
+                        const T p0 = P[e];
+                        T un = 0, d = 0;
+                        if (c == FREE) {
+                            const T wxm = Wx[e - 1], wxp = Wx[e], wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e],
+                                    wzp = Wzh[e];
+                            d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
+                            const T nb = ((wxm * P[e - 1] + wxp * P[e + 1]) + (wym * P[e - W2] + wyp * P[e + W2])) +
+                                         (wzm * Pl[e] + wzp * Ph[e]);
+                            const T s = d * p0 - nb;
+                            if (d > (T)0) un = sUk[m2 * R2 + e] - alpha * s / d;
+                        }
+                        sUn[m3 * R2 + e] = un;
+                        if (zint && jx >= 2 && jx < TX + 2 && jy >= 2 && jy < TY + 2) {
+                            const int gx = ox + jx - 2, gy = oy + jy - 2;
+                            if (gx < ex && gy < ey) {
+                                const int64_t i = base + ((int64_t)zm * ny + gy) * nx + gx;
+                                Uout[i] = un;
+                                Pout[i] = p0;
+                                if (c == FREE) {
+                                    X[i] = X[i] + alpha * p0;
+                                    const acc du = (acc)d * (acc)un;
+                                    a_gam += du * (acc)un;
+                                    a_rr += du * du;
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                // -- C: plane zw = zf-2 interior, delta = (u, A u)
+                const int zw = zf - 2;
+                if (zw >= z0 && zw < z1) {
+                    const int w3 = (zw + 6) % 3, w4 = (zw + 8) & 3, wn4 = (zw + 9) & 3;
+                    const T* U = sUn + w3 * R2;
+                    const T* Ul = sUn + ((zw + 5) % 3) * R2;
+                    const T* Uh = sUn + ((zw + 7) % 3) * R2;
+                    const T* Wx = sWx + w4 * R2;
+                    const T* Wy = sWy + w4 * R2;
+                    const T* Wzl = sWz + w4 * R2;
+                    const T* Wzh = sWz + wn4 * R2;
+                    for (int e0 = tid; e0 < TX * TY; e0 += NT) {
+                        const int jx = e0 % TX + 2, jy = e0 / TX + 2;
+                        const int e = jy * W2 + jx;
+                        const T u0 = U[e];
+                        if (u0 != (T)0 && ox + jx - 2 < ex && oy + jy - 2 < ey) {
+                            const T wxm = Wx[e - 1], wxp = Wx[e], wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e],
+                                    wzp = Wzh[e];
+                            const T d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
+                            const T nb = ((wxm * U[e - 1] + wxp * U[e + 1]) + (wym * U[e - W2] + wyp * U[e + W2])) +
+                                         (wzm * Ul[e] + wzp * Uh[e]);
+                            a_del += (acc)u0 * (acc)(d * u0 - nb);
+                        }
+                    }
+                }
+            }
+        }
+        // -- reductions: block (FP64), then the last CTA of the system
+        double v0 = (double)a_gam, v1 = (double)a_rr, v2 = (double)a_del;
+        block_reduce3<NT>(v0, v1, v2, red);
+        if (tid == 0) {
+            double* pp = A.partials + ((int64_t)box * tpb + t) * 3;
+            pp[0] = v0;
+            pp[1] = v1;
+            pp[2] = v2;
+            __threadfence();
+            const unsigned prev = atomicAdd(&S->counter, 1u);
+            s_last = (prev == (unsigned)tpb - 1u);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double t0 = 0, t1 = 0, t2 = 0;
+            const double* pb = A.partials + (int64_t)box * tpb * 3;
+            for (int k = tid; k < tpb; k += NT) {
+                t0 += __ldcg(pb + 3 * k);
+                t1 += __ldcg(pb + 3 * k + 1);
+                t2 += __ldcg(pb + 3 * k + 2);
+            }
+            block_reduce3<NT>(t0, t1, t2, red);
+            if (tid == 0) {
+                S->counter = 0u;
+                finalize_box(S, t0, t1, t2, A.n_active);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace rwk

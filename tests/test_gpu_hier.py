@@ -1,0 +1,172 @@
+"""Parity of the CUDA pyramid and hierarchical procedure (rw_build_pyramid,
+rw_refine_level, rw_update_seeds) with the oracle's H_p."""
+import numpy as np
+import pytest
+
+import oracle as O
+import phantoms as P
+from oracle import hrw
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+NEAR = 1e-4      # a pruning decision may differ only this close to its threshold
+
+
+@pytest.fixture(scope="module")
+def rw():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2103_09564_gb300 as m
+    m.load()
+    return m
+
+
+def _near_threshold(ni, opts):
+    return (abs((ni.mx - ni.mn) - opts.t_hom) < NEAR or abs((ni.mn - 0.5) - opts.t_bin) < NEAR or
+            abs((0.5 - ni.mx) - opts.t_bin) < NEAR)
+
+
+def _compare(rw, tree, otree, opts, s, incremental=False):
+    """Compare level by level: node sets and decisions must agree unless the
+    oracle's statistic sits within NEAR of a threshold; fields within TOL
+    outside subtrees below such near-threshold nodes."""
+    K = len(otree.P) - 1
+    excluded = []     # (level, brick) roots of subtrees where decisions may differ
+    for k in range(K + 1):
+        fl, mn, mx, md = tree.node_stats(k)
+        gpu_solved = {tuple(int(v) for v in b) for b in np.argwhere(fl & rw.RW_NODE_SOLVED)}
+        or_solved = {b for b, ni in otree.info[k].items() if ni.solved}
+
+        def under_excluded(b):
+            for (kk, e) in excluded:
+                sh = k - kk
+                if tuple(v >> sh for v in b) == e:
+                    return True
+            return False
+        for b in gpu_solved ^ or_solved:
+            assert under_excluded(b), f"level {k}: node {b} solved on one side only"
+        for b in gpu_solved & or_solved:
+            if under_excluded(b):
+                continue
+            ni = otree.info[k][b]
+            gp = bool(fl[b] & rw.RW_NODE_PRUNABLE)
+            if gp != ni.prunable:
+                assert _near_threshold(ni, opts), f"level {k}: prunable differs at {b}"
+                excluded.append((k, b))
+            if incremental:
+                gs = bool(fl[b] & rw.RW_NODE_SIMILAR)
+                if gs != ni.similar:
+                    assert abs(ni.maxdiff - opts.t_inc) < NEAR, f"level {k}: similar differs at {b}"
+                    excluded.append((k, b))
+        field = tree.read_level(k).astype(np.float64)
+        mask = np.ones(field.shape, bool)
+        for (kk, e) in excluded:
+            sh = k - kk
+            lo = [v * s * (1 << sh) for v in e]
+            hi = [(v + 1) * s * (1 << sh) for v in e]
+            # the upsampling of the next levels reaches one parent voxel further
+            mask[max(lo[0] - 2 * s, 0):hi[0] + 2 * s, max(lo[1] - 2 * s, 0):hi[1] + 2 * s,
+                 max(lo[2] - 2 * s, 0):hi[2] + 2 * s] = False
+        err = np.max(np.abs(field - otree.P[k])[mask]) if mask.any() else 0.0
+        assert err <= TOL, f"level {k}: max |gpu - oracle| = {err}"
+    return excluded
+
+
+def test_pyramid_bit_exact(rw):
+    ph = P.vessel_tree(shape=(37, 50, 70), seed=5, n_segments=10)
+    pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    lv = O.pyramid(O.leaf_level(q), 8)
+    assert pyr.levels == len(lv)
+    for k in range(len(lv)):
+        assert np.array_equal(pyr.read_level(k), lv[k]), k
+
+
+@pytest.mark.parametrize("n,s,seed", [(64, 8, 2), (96, 16, 3), ((40, 72, 56), 8, 4)])
+def test_full_run_parity(rw, n, s, seed):
+    if isinstance(n, tuple):
+        ph = P.vessel_tree(shape=n, seed=seed, n_segments=25)
+    else:
+        ph = P.vessel_tree(n=n, seed=seed, n_segments=30)
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    opts = rw.Opts(brick_size=s, beta=130.0, tol=1e-9)
+    tree = rw.Tree(pyr, opts)
+    st = tree.run(ph["labels_xyz"], ph["labels_value"])
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), s)
+    oo = hrw.Opts(brick_size=s, beta=130.0)
+    ot = hrw.run(levels, ph["labels_xyz"], ph["labels_value"], oo)
+    exc = _compare(rw, tree, ot, oo, s)
+    if not exc:
+        assert st["bricks_solved"] == ot.stats["bricks_solved"]
+        assert st["bricks_pruned"] == ot.stats["bricks_pruned"]
+
+
+def test_single_brick_equals_plain(rw):
+    c = P.random_case((12, 10, 14), seed=5, seed_frac=0.05, levels=[0.0, 1.0])
+    z, y, x = np.nonzero(c["code"] == 1)
+    xyz = np.stack([x + 0.5, y + 0.5, z + 0.5], 1)
+    val = c["value"][z, y, x]
+    pyr = rw.rw_build_pyramid(c["volume"], 16)
+    tree = rw.Tree(pyr, rw.Opts(brick_size=16, beta=30.0, tol=1e-11))
+    tree.run(xyz, val)
+    leaf = O.leaf_level(O.quantize(c["volume"]))
+    xo, _, _, _ = O.rw_solve(leaf.astype(np.float64), c["code"], c["value"], 30.0)
+    assert np.max(np.abs(tree.read_level(0) - xo)) <= 1e-6
+
+
+def test_no_pruning_parity_and_agreement(rw):
+    ph = P.vessel_tree(n=64, seed=6, n_segments=30)
+    pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    t1 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9, prune_hom=0, prune_dt=0))
+    t1.run(ph["labels_xyz"], ph["labels_value"])
+    t2 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9))
+    s2 = t2.run(ph["labels_xyz"], ph["labels_value"])
+    a, b = t1.read_level(pyr.levels - 1), t2.read_level(pyr.levels - 1)
+    assert s2["bricks_pruned"] > 0
+    assert np.mean((a > 0.5) == (b > 0.5)) >= 0.999
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=130.0, prune_hom=False, prune_dt=False)
+    ot = hrw.run(levels, ph["labels_xyz"], ph["labels_value"], oo)
+    _compare(rw, t1, ot, oo, 8)
+
+
+def test_incremental_update_parity(rw):
+    ph = P.vessel_tree(n=64, seed=7, n_segments=30)
+    n0 = len(ph["labels_value"]) - 6
+    pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-9)
+    tree = rw.Tree(pyr, opts)
+    tree.run(ph["labels_xyz"][:n0], ph["labels_value"][:n0])
+    su = tree.update_seeds(ph["labels_xyz"][n0:], ph["labels_value"][n0:])
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=130.0)
+    ot = hrw.run(levels, ph["labels_xyz"][:n0], ph["labels_value"][:n0], oo)
+    ou = hrw.update(ot, ph["labels_xyz"][n0:], ph["labels_value"][n0:])
+    exc = _compare(rw, tree, ou, oo, 8, incremental=True)
+    if not exc:
+        assert su["bricks_solved"] == ou.stats["bricks_solved"]
+        assert su["bricks_reused"] == ou.stats["bricks_reused"]
+
+
+def test_update_without_labels_keeps_everything(rw):
+    ph = P.vessel_tree(n=32, seed=3, n_segments=10)
+    pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9))
+    tree.run(ph["labels_xyz"], ph["labels_value"])
+    before = tree.read_level(pyr.levels - 1).copy()
+    su = tree.update_seeds(np.zeros((0, 3)), np.zeros(0))
+    assert su["bricks_solved"] == 1
+    assert np.array_equal(tree.read_level(pyr.levels - 1), before)
+
+
+def test_per_brick_sequential_equals_batched(rw):
+    ph = P.vessel_tree(n=64, seed=8, n_segments=20)
+    pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    a = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9))
+    a.run(ph["labels_xyz"], ph["labels_value"])
+    b = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9, batch_bricks=0, precision="fp64"))
+    b.run(ph["labels_xyz"], ph["labels_value"])
+    assert np.max(np.abs(a.read_level(pyr.levels - 1) - b.read_level(pyr.levels - 1))) <= TOL
