@@ -29,11 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "voxel-CG-iterations/s and HBM GB/s (% of peak) at <=1e-4 prob error vs FP64"
 UNIT = "voxel-iter/s"
-N = 256
+N = int(os.environ.get("RW_BENCH_N", "256"))
 BETA = 130.0
 TOL = 1e-8
 SWEEP_BYTES_PER_VOXEL = 27   # x(delta) r+w 8, u r+w 8, p r+w 8, g 2, code 1  (FP32 vectors, unorm16 g)
-WORKLOAD = "plain random walker, 256^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
+WORKLOAD = f"plain random walker, {N}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
 
 
 def _peaks():
@@ -215,7 +215,7 @@ def run(args):
     code_h = np.ascontiguousarray(c["code"])
     val_h = np.ascontiguousarray(c["value"])
     out_h = np.empty_like(vol_h)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(0, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     vi_e2e = 0
@@ -223,7 +223,7 @@ def run(args):
         _, st = rw.rw_solve(vol_h, code_h, val_h, opts, out=out_h)
         vi_e2e += st["voxel_iters"]
     t_e2e = time.perf_counter() - t0
-    e2e = {"value": vi_e2e / t_e2e, "unit": UNIT,
+    e2e = {"value": vi_e2e / t_e2e if e2e_steps else None, "unit": UNIT,
            "h2d_bytes_per_step": int(vol_h.nbytes + code_h.nbytes + val_h.nbytes),
            "d2h_bytes_per_step": int(out_h.nbytes)}
 
@@ -264,6 +264,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

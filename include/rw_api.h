@@ -117,7 +117,7 @@ typedef struct rw_opts {
 } rw_opts;
 
 enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, RW_TILE_40x20 = 4,
-       RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7 };
+       RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7, RW_TILE_32x32 = 8, RW_TILE_64x16 = 9 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */
@@ -135,6 +135,10 @@ typedef struct rw_stats {
     double ms_solve;        /* time inside the PCG loops */
     double ms_sweeps;       /* device time of the fused sweeps (CUDA events on the library stream) */
     int64_t launches;       /* kernels launched by the call */
+    int32_t tile;           /* sweep tile used last (RW_TILE_*) */
+    int32_t iters_per_graph;/* sweeps per CUDA graph used last */
+    int64_t not_converged;  /* systems left above tol (bricks keep their best iterate) */
+    int64_t fp64_fallbacks; /* solves that finished with FP64 sweeps */
 } rw_stats;
 
 typedef struct rw_pyramid rw_pyramid;

@@ -17,7 +17,8 @@ RW_MIXED, RW_FP64 = 0, 1
 RW_CODE_FREE, RW_CODE_SEED, RW_CODE_ABSENT = 0, 1, 2
 RW_NODE_SOLVED, RW_NODE_PRUNABLE, RW_NODE_HOM, RW_NODE_DT, RW_NODE_CFL, RW_NODE_SIMILAR, RW_NODE_REUSED, \
     RW_NODE_CFL_ADDED, RW_NODE_NO_SEEDS = 1, 2, 4, 8, 16, 32, 64, 128, 256
-RW_TILE = {"auto": 0, "32x16": 1, "64x8": 2, "40x8": 3, "40x20": 4, "80x8": 5, "80x16": 6, "32x8": 7}
+RW_TILE = {"auto": 0, "32x16": 1, "64x8": 2, "40x8": 3, "40x20": 4, "80x8": 5, "80x16": 6, "32x8": 7, "32x32": 8,
+           "64x16": 9}
 
 # every function declared in include/rw_api.h
 EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspace", "rw_solve", "rw_solve_adjoint",
@@ -54,7 +55,8 @@ class rw_stats(ctypes.Structure):
                 ("bricks_solved", ctypes.c_int64), ("bricks_pruned", ctypes.c_int64),
                 ("bricks_reused", ctypes.c_int64), ("bricks_conflict", ctypes.c_int64), ("sweeps", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("ms_solve", ctypes.c_double), ("ms_sweeps", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("tile", ctypes.c_int32), ("iters_per_graph", ctypes.c_int32),
+                ("not_converged", ctypes.c_int64), ("fp64_fallbacks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

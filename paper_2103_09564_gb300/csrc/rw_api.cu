@@ -68,7 +68,7 @@ double now_ms() {
 enum Slot {
     S_G, S_U0, S_U1, S_P0, S_P1, S_DELTA, S_XHI, S_PART, S_RPART, S_SC, S_NACT, S_VOL, S_CODE, S_VAL, S_X0, S_OUT,
     S_RHS, S_EXT, S_JOBS, S_LAB, S_BFLAGS, S_STATS, S_POOL_G, S_POOL_CODE, S_POOL_X, S_ADJ_PART, S_DBETA, S_DG,
-    S_XF, S_STATUS, S_COUNT
+    S_XF, S_STATUS, S_GC, S_COUNT
 };
 
 struct DevWorkspace {
@@ -162,7 +162,7 @@ rw_status leave(DevWorkspace* w) {
 
 rw_status check_opts(const rw_opts& o) {
     if (!(o.beta >= 0.0f) || !(o.w_min >= 0.0f) || !(o.tol >= 0.0) || o.max_iter < 1 || o.refine_rounds < 0 ||
-        (o.precision != RW_MIXED && o.precision != RW_FP64) || o.iters_per_graph < 2 || o.tile < 0 || o.tile > 7 ||
+        (o.precision != RW_MIXED && o.precision != RW_FP64) || o.iters_per_graph < 2 || o.tile < 0 || o.tile >= N_TILES ||
         o.brick_size < 2 || !(o.expand >= 1.0f) || o.max_batch < 1)
         return fail(RW_ERR_INVALID_ARG, "invalid rw_opts");
     return RW_OK;
@@ -192,16 +192,15 @@ std::map<std::string, std::pair<int, int>> g_tuned;  // class -> (tile, iters pe
 
 std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     std::vector<int> c;
+    (void)gtype;
     if (fp64) {
         c = {7, 3};
-    } else if (gtype == G_U16) {
-        c = {1, 2, 7};
     } else if (nx <= 48) {
-        c = {3, 4, 7, 1};
+        c = {3, 4, 7};
     } else if (nx <= 96 && nx % 80 == 0) {
-        c = {5, 6, 1, 2};
+        c = {5, 6, 9};
     } else {
-        c = {1, 2, 7, 6};
+        c = {1, 8, 9, 2, 7};
     }
     std::vector<int> ok;
     for (int t : c)
@@ -263,6 +262,7 @@ struct SolveResult {
     double ms_sweeps = 0.0;   // device time of the graph-launched sweeps
     int tile = 0;
     int ipg = 0;
+    int fp64_fallback = 0;
 };
 
 rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* const u[2], void* const p[2],
@@ -344,58 +344,109 @@ rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* co
     return RW_OK;
 }
 
-rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, SolveResult* R) {
-    const int fp64 = o.precision == RW_FP64 ? 1 : 0;
-    const Boxes& bx = P.bx;
-    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
-    const int64_t ntot = nvox * bx.nbox;
-    const size_t tsz = fp64 ? 8 : 4;
-    void *u[2], *p[2];
-    float* delta = nullptr;
-    BoxScalars* sc = nullptr;
-    int* nact = nullptr;
-    double *rpart = nullptr, *part = nullptr;
-    RCK(ws_get(w, S_U0, ntot * tsz, &u[0]));
-    RCK(ws_get(w, S_U1, ntot * tsz, &u[1]));
-    RCK(ws_get(w, S_P0, ntot * tsz, &p[0]));
-    RCK(ws_get(w, S_P1, ntot * tsz, &p[1]));
-    if (!fp64) RCK(ws_get_t(w, S_DELTA, ntot * 4, &delta));
-    RCK(ws_get_t(w, S_SC, bx.nbox * sizeof(BoxScalars), &sc));
-    RCK(ws_get_t(w, S_NACT, 64, &nact));
-    const int bpb = (int)((nvox + 255) / 256);
-    RCK(ws_get_t(w, S_RPART, (size_t)bx.nbox * bpb * 4 * sizeof(double), &rpart));
-
-    // configuration: cached autotuned choice, an explicit tile, or a default
-    const std::string key = class_key(fp64, P.gtype, bx);
-    std::vector<int> cands = tile_candidates(fp64, P.gtype, bx.nx);
-    if (cands.empty()) return fail(RW_ERR_INVALID_ARG, "no sweep kernel for this precision/storage");
-    int tile = cands[0];
-    int ipg = std::max(2, o.iters_per_graph & ~1);
+// Per-precision sweep set-up: buffers of the vector type, a configuration
+// (autotuned once per problem class), partial-sum storage.
+struct PrecState {
+    int fp64 = 0;
+    void* u[2] = {nullptr, nullptr};
+    void* p[2] = {nullptr, nullptr};
+    SweepCfg cfg;
+    std::vector<int> cands;
+    std::string key;
     bool tune = false;
-    if (o.tile != RW_TILE_AUTO) {
+};
+
+rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, int fp64, PrecState* ps,
+                     double** part) {
+    const Boxes& bx = P.bx;
+    const int64_t ntot = (int64_t)bx.nx * bx.ny * bx.nz * bx.nbox;
+    const size_t tsz = fp64 ? 8 : 4;
+    ps->fp64 = fp64;
+    RCK(ws_get(w, S_U0, ntot * tsz, &ps->u[0]));
+    RCK(ws_get(w, S_U1, ntot * tsz, &ps->u[1]));
+    RCK(ws_get(w, S_P0, ntot * tsz, &ps->p[0]));
+    RCK(ws_get(w, S_P1, ntot * tsz, &ps->p[1]));
+    ps->key = class_key(fp64, P.gtype, bx);
+    ps->cands = tile_candidates(fp64, P.gtype, bx.nx);
+    if (ps->cands.empty()) return fail(RW_ERR_INVALID_ARG, "no sweep kernel for this precision/storage");
+    int tile = ps->cands[0];
+    int ipg = std::max(2, o.iters_per_graph & ~1);
+    ps->tune = false;
+    if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0) {
         tile = o.tile;
-    } else {
-        auto it = g_tuned.find(key);
+    } else if (o.tile == RW_TILE_AUTO) {
+        auto it = g_tuned.find(ps->key);
         if (it != g_tuned.end()) {
             tile = it->second.first;
             ipg = it->second.second;
         } else {
-            tune = true;
+            ps->tune = ps->cands.size() > 1;
         }
     }
-    SweepCfg cfg;
-    RCK(make_cfg(fp64, P.gtype, tile, bx, w->sms, ipg, &cfg));
-    size_t part_elems = 0;
-    for (int t : cands) {
+    RCK(make_cfg(fp64, P.gtype, tile, bx, w->sms, ipg, &ps->cfg));
+    size_t part_elems = (size_t)bx.nbox * ps->cfg.ntx * ps->cfg.nty * ps->cfg.nzc * 3;
+    for (int t : ps->cands) {
         SweepCfg c2;
         RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2));
         part_elems = std::max(part_elems, (size_t)bx.nbox * c2.ntx * c2.nty * c2.nzc * 3);
     }
-    {
-        size_t own = (size_t)bx.nbox * cfg.ntx * cfg.nty * cfg.nzc * 3;
-        part_elems = std::max(part_elems, own);
+    RCK(ws_get_t(w, S_PART, part_elems * sizeof(double), part));
+    return RW_OK;
+}
+
+// Autotuner: on the first round of a new problem class, time 4 sweeps of
+// every candidate tile on the live state (real PCG iterations; an even count
+// keeps the buffer parity), keep the fastest and size the graph chunk to about
+// 1 ms of sweeps.
+rw_status autotune(DevWorkspace* w, const SolveProblem& P, PrecState* ps, const SweepArgs& sa, SolveResult* R) {
+    float best = 1e30f;
+    int best_tile = ps->cfg.tile;
+    for (int t : ps->cands) {
+        SweepCfg c2;
+        RCK(make_cfg(ps->fp64, P.gtype, t, P.bx, w->sms, ps->cfg.ipg, &c2));
+        SweepArgs s2 = sa;
+        s2.ntx = c2.ntx;
+        s2.nty = c2.nty;
+        s2.nzc = c2.nzc;
+        s2.zc = c2.zc;
+        float ms = 0;
+        RCK(time_tile(w, c2, s2, ps->u, ps->p, ps->fp64, P.gtype, 4, &ms));
+        R->sweeps += 4;
+        if (ms < best) {
+            best = ms;
+            best_tile = t;
+        }
     }
-    RCK(ws_get_t(w, S_PART, part_elems * sizeof(double), &part));
+    const float per = best / 4.0f;
+    int k = (int)std::lround(1.0 / std::max(per, 1e-4f));
+    k = std::max(8, std::min(64, k)) & ~1;
+    RCK(make_cfg(ps->fp64, P.gtype, best_tile, P.bx, w->sms, k, &ps->cfg));
+    g_tuned[ps->key] = std::make_pair(best_tile, k);
+    ps->tune = false;
+    return RW_OK;
+}
+
+// Solve every box of P.  Mixed precision: FP32 PCG rounds on the correction,
+// each ended by an FP64 residual of x_hi.  A system whose round does not cut
+// its true residual by 10x is beyond what FP32 sweeps can resolve (its
+// condition number approaches 1/eps_fp32); the remaining work then runs with
+// FP64 sweeps on x_hi (one extra round, to tol).
+rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, SolveResult* R) {
+    const Boxes& bx = P.bx;
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    const int64_t ntot = nvox * bx.nbox;
+    int cur64 = o.precision == RW_FP64 ? 1 : 0;
+    float* delta = nullptr;
+    BoxScalars* sc = nullptr;
+    int* nact = nullptr;
+    double *rpart = nullptr, *part = nullptr;
+    if (!cur64) RCK(ws_get_t(w, S_DELTA, ntot * 4, &delta));
+    RCK(ws_get_t(w, S_SC, bx.nbox * sizeof(BoxScalars), &sc));
+    RCK(ws_get_t(w, S_NACT, 64, &nact));
+    const int bpb = (int)((nvox + 255) / 256);
+    RCK(ws_get_t(w, S_RPART, (size_t)bx.nbox * bpb * 4 * sizeof(double), &rpart));
+    PrecState ps;
+    RCK(prec_setup(w, P, o, cur64, &ps, &part));
 
     ResidArgs ra;
     ra.bx = bx;
@@ -406,24 +457,30 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     ra.x0 = P.x0;
     ra.rhs = P.rhs;
     ra.x = P.x_hi;
-    ra.u = u[0];
-    ra.p = p[0];
+    ra.u = ps.u[0];
+    ra.p = ps.p[0];
     ra.part = rpart;
     ra.blocks_per_box = bpb;
     ra.mbeta = -(double)o.beta;
     ra.wmin = (double)o.w_min;
 
+    uint32_t* gc = nullptr;
+    if (!cur64) {
+        RCK(ws_get_t(w, S_GC, ntot * 4, &gc));
+        CK(counted(launch_pack_gc(bx, P.g, P.gtype, P.code, gc, w->stream)));
+    }
     CK(cudaMemsetAsync(sc, 0, bx.nbox * sizeof(BoxScalars), w->stream));
-    if (P.init_x) CK(counted(launch_init_x(fp64, ra, w->stream)));
-    CK(counted(launch_residual(fp64, ra, delta, w->stream)));
+    if (P.init_x) CK(counted(launch_init_x(cur64, ra, w->stream)));
+    CK(counted(launch_residual(cur64, ra, delta, w->stream)));
     CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 1, w->stream)));
-    CK(counted(launch_zero_homog(fp64, bx, P.code, sc, P.x_hi, w->stream)));
+    CK(counted(launch_zero_homog(cur64, bx, P.code, sc, P.x_hi, w->stream)));
 
     SweepArgs sa;
     sa.bx = bx;
     sa.g = P.g;
     sa.code = P.code;
-    sa.x = fp64 ? (void*)P.x_hi : (void*)delta;
+    sa.gc = gc;
+    sa.x = cur64 ? (void*)P.x_hi : (void*)delta;
     sa.sc = sc;
     sa.partials = part;
     sa.n_active = nact;
@@ -432,60 +489,61 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     sa.mbeta = -(double)o.beta;
     sa.wmin = (double)o.w_min;
 
-    const int rounds = fp64 ? 1 : std::max(1, o.refine_rounds);
-    const double eps_inner = fp64 ? 0.0 : 1e-5;
+    const int mixed_rounds = std::max(1, o.refine_rounds);
+    int max_rounds = cur64 ? 1 : mixed_rounds;
+    std::vector<BoxScalars> h(bx.nbox);
+    std::vector<double> prev(bx.nbox, -1.0);
     const double t0 = now_ms();
-    for (int r = 0; r < rounds; ++r) {
+    for (int r = 0; r < max_rounds; ++r) {
+        const double eps_inner = cur64 ? 0.0 : 1e-5;
         CK(cudaMemsetAsync(nact, 0, sizeof(int), w->stream));
         CK(counted(launch_start_round(sc, bx.nbox, r, o.tol, eps_inner, o.max_iter, nact, w->stream)));
+        CK(cudaMemcpyAsync(h.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaMemcpyAsync(w->pinned, nact, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaStreamSynchronize(w->stream));
         if (*w->pinned == 0) break;
+        for (int b = 0; b < bx.nbox; ++b) prev[b] = h[b].rr_true;
         R->rounds = r + 1;
-        if (tune) {
-            // autotune on the first round of a new problem class: 4 sweeps per
-            // candidate tile, keep the fastest; sweeps per graph target ~1 ms
-            float best = 1e30f;
-            int best_tile = tile;
-            for (int t : cands) {
-                SweepCfg c2;
-                RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2));
-                SweepArgs s2 = sa;
-                s2.ntx = c2.ntx;
-                s2.nty = c2.nty;
-                s2.nzc = c2.nzc;
-                s2.zc = c2.zc;
-                float ms = 0;
-                RCK(time_tile(w, c2, s2, u, p, fp64, P.gtype, 4, &ms));
-                R->sweeps += 4;
-                if (ms < best) {
-                    best = ms;
-                    best_tile = t;
-                }
-            }
-            const float per = best / 4.0f;
-            int k = (int)std::lround(1.0 / std::max(per, 1e-4f));
-            k = std::max(8, std::min(64, k)) & ~1;
-            RCK(make_cfg(fp64, P.gtype, best_tile, bx, w->sms, k, &cfg));
-            g_tuned[key] = std::make_pair(best_tile, k);
-            tune = false;
-        }
-        sa.ntx = cfg.ntx;
-        sa.nty = cfg.nty;
-        sa.nzc = cfg.nzc;
-        sa.zc = cfg.zc;
-        const int64_t cap = R->sweeps + (int64_t)o.max_iter + 4 * cfg.ipg;
-        RCK(run_graph_chunks(w, cfg, sa, u, p, fp64, P.gtype, nact, &R->sweeps, cap, &R->ms_sweeps));
-        if (!fp64) CK(counted(launch_accumulate(ntot, P.code, delta, P.x_hi, w->stream)));
-        CK(counted(launch_residual(fp64, ra, delta, w->stream)));
+        sa.partials = part;
+        if (ps.tune) RCK(autotune(w, P, &ps, sa, R));
+        sa.ntx = ps.cfg.ntx;
+        sa.nty = ps.cfg.nty;
+        sa.nzc = ps.cfg.nzc;
+        sa.zc = ps.cfg.zc;
+        const int64_t cap = R->sweeps + (int64_t)o.max_iter + 4 * ps.cfg.ipg;
+        RCK(run_graph_chunks(w, ps.cfg, sa, ps.u, ps.p, cur64, P.gtype, nact, &R->sweeps, cap, &R->ms_sweeps));
+        if (!cur64) CK(counted(launch_accumulate(ntot, P.code, delta, P.x_hi, w->stream)));
+        CK(counted(launch_residual(cur64, ra, delta, w->stream)));
         CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
+        if (!cur64) {
+            CK(cudaMemcpyAsync(h.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
+            CK(cudaStreamSynchronize(w->stream));
+            bool stagnated = false;
+            for (int b = 0; b < bx.nbox; ++b) {
+                const BoxScalars& S = h[b];
+                if (S.nseed == 0 || S.nfree == 0 || !(S.bb > 0.0)) continue;
+                if (S.rr_true > o.tol * o.tol * S.bb && prev[b] > 0.0 && S.rr_true > 1e-2 * prev[b]) stagnated = true;
+            }
+            if (stagnated) {
+                // switch to FP64 sweeps for one final round
+                cur64 = 1;
+                RCK(prec_setup(w, P, o, 1, &ps, &part));
+                ra.u = ps.u[0];
+                ra.p = ps.p[0];
+                sa.x = P.x_hi;
+                CK(counted(launch_residual(1, ra, nullptr, w->stream)));
+                CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
+                max_rounds = r + 2;
+                R->fp64_fallback = 1;
+            }
+        }
     }
     R->sc.resize(bx.nbox);
     CK(cudaMemcpyAsync(R->sc.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
     CK(cudaStreamSynchronize(w->stream));
     R->ms_solve = now_ms() - t0;
-    R->tile = cfg.tile;
-    R->ipg = cfg.ipg;
+    R->tile = ps.cfg.tile;
+    R->ipg = ps.cfg.ipg;
     return RW_OK;
 }
 
@@ -517,6 +575,10 @@ void stats_from(const SolveResult& R, const rw_opts& o, rw_stats* st, int* n_unc
         st->sweeps += R.sweeps;
         st->ms_solve += R.ms_solve;
         st->ms_sweeps += R.ms_sweeps;
+        st->tile = R.tile;
+        st->iters_per_graph = R.ipg;
+        st->not_converged += bad;
+        st->fp64_fallbacks += R.fp64_fallback;
     }
     if (n_unconverged) *n_unconverged = bad;
     if (n_noseed) *n_noseed = nos;

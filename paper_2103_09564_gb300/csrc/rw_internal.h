@@ -39,8 +39,9 @@ struct Boxes {
 struct SweepArgs {
     Boxes bx;
     int ntx, nty, nzc, zc;  // tiles per box: x, y, z-chunks; chunk depth
-    const void* g;          // intensities (uint16 unorm or float)
-    const uint8_t* code;
+    const void* g;          // intensities (uint16 unorm or float), FP64 sweep
+    const uint8_t* code;    // seed codes, FP64 sweep
+    const uint32_t* gc;     // packed FP32 g | code (0 absent, 1 free, 2 seed), FP32 sweep
     void* x;                // iterate (T)
     const void* u_in;       // u_k   (T)
     const void* p_in;       // p_k-1 (T)
@@ -57,7 +58,8 @@ struct SweepArgs {
 
 enum GType { G_U16 = 0, G_F32 = 1 };
 enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE_80x8 = 5, TILE_80x16 = 6,
-              TILE_32x8 = 7 };
+              TILE_32x8 = 7, TILE_32x32 = 8, TILE_64x16 = 9 };
+constexpr int N_TILES = 10;
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
 // combination that is not instantiated.
@@ -95,6 +97,9 @@ cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, 
 cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, const BoxScalars* sc, void* x,
                               cudaStream_t s);
 cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s);
+// Pack g and the seed code of every voxel into one word for the FP32 sweep.
+cudaError_t launch_pack_gc(const Boxes& bx, const void* g, int gtype, const uint8_t* code, uint32_t* gc,
+                           cudaStream_t s);
 
 // Normalisation / quantisation (hier_kernels.cu).
 cudaError_t launch_quantize(const void* v, int dtype, int64_t n, float lo, float hi, int normalize, int storage,

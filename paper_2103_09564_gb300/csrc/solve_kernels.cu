@@ -11,16 +11,14 @@
 
 namespace rwk {
 
-cudaError_t sweep_launch_f32_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
-cudaError_t sweep_launch_f32_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep2_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep2_prepare(int tile);
+int sweep2_occupancy(int tile);
+size_t sweep2_smem(int tile);
 cudaError_t sweep_launch_d64_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_launch_d64_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
-cudaError_t sweep_prepare_f32_u16(int tile);
-cudaError_t sweep_prepare_f32_f32(int tile);
 cudaError_t sweep_prepare_d64_u16(int tile);
 cudaError_t sweep_prepare_d64_f32(int tile);
-int sweep_occupancy_f32_u16(int tile);
-int sweep_occupancy_f32_f32(int tile);
 int sweep_occupancy_d64_u16(int tile);
 int sweep_occupancy_d64_f32(int tile);
 
@@ -29,15 +27,15 @@ cudaError_t sweep_prepare(int fp64, int gtype, int tile);
 // Resident CTAs per SM of an instantiated sweep (0 when the combination is
 // not compiled); opts the kernel in to its dynamic shared memory first.
 int sweep_occupancy(int fp64, int gtype, int tile) {
-    static int cache[2][2][8];
+    static int cache[2][2][N_TILES];
     static bool init = false;
     if (!init) {
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
-                for (int c = 0; c < 8; ++c) cache[a][b][c] = -1;
+                for (int c = 0; c < N_TILES; ++c) cache[a][b][c] = -1;
         init = true;
     }
-    if (tile < 1 || tile > 7) return 0;
+    if (tile < 1 || tile >= N_TILES) return 0;
     int& slot = cache[fp64 ? 1 : 0][gtype == G_U16 ? 0 : 1][tile];
     if (slot >= 0) return slot;
     if (sweep_prepare(fp64, gtype, tile) != cudaSuccess) {
@@ -46,37 +44,41 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
         return 0;
     }
     if (fp64) slot = gtype == G_U16 ? sweep_occupancy_d64_u16(tile) : sweep_occupancy_d64_f32(tile);
-    else slot = gtype == G_U16 ? sweep_occupancy_f32_u16(tile) : sweep_occupancy_f32_f32(tile);
+    else slot = sweep2_occupancy(tile);
     return slot;
 }
 
+
 void tile_dims(int tile, int* tx, int* ty) {
-    static const int T[8][2] = {{0, 0}, {32, 16}, {64, 8}, {40, 8}, {40, 20}, {80, 8}, {80, 16}, {32, 8}};
-    if (tile < 1 || tile > 7) tile = 1;
+    static const int T[N_TILES][2] = {{0, 0}, {32, 16}, {64, 8}, {40, 8}, {40, 20}, {80, 8}, {80, 16}, {32, 8},
+                                      {32, 32}, {64, 16}};
+    if (tile < 1 || tile >= N_TILES) tile = 1;
     *tx = T[tile][0];
     *ty = T[tile][1];
 }
 
 int sweep_threads(int tile) {
-    static const int N[8] = {0, 512, 512, 320, 800, 640, 640, 256};
-    return (tile >= 1 && tile <= 7) ? N[tile] : 0;
+    static const int N[N_TILES] = {0, 512, 512, 320, 800, 640, 640, 256, 1024, 1024};
+    return (tile >= 1 && tile < N_TILES) ? N[tile] : 0;
 }
 
+// FP64 sweeps use the generic kernel (sweep_kernel.cuh); FP32 sweeps the
+// pipelined one (sweep2_kernel.cuh), which reads the packed g|code words.
 size_t sweep_smem_bytes(int fp64, int tile) {
     int tx, ty;
     tile_dims(tile, &tx, &ty);
     const int r2 = (tx + 4) * (ty + 4);
-    return fp64 ? (size_t)sweep_planes_bytes<double>(r2) : (size_t)sweep_planes_bytes<float>(r2);
+    return fp64 ? (size_t)sweep_planes_bytes<double>(r2) : sweep2_smem(tile);
 }
 
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     if (fp64) return gtype == G_U16 ? sweep_launch_d64_u16(tile, a, grid, s) : sweep_launch_d64_f32(tile, a, grid, s);
-    return gtype == G_U16 ? sweep_launch_f32_u16(tile, a, grid, s) : sweep_launch_f32_f32(tile, a, grid, s);
+    return sweep2_launch(tile, a, grid, s);
 }
 
 cudaError_t sweep_prepare(int fp64, int gtype, int tile) {
     if (fp64) return gtype == G_U16 ? sweep_prepare_d64_u16(tile) : sweep_prepare_d64_f32(tile);
-    return gtype == G_U16 ? sweep_prepare_f32_u16(tile) : sweep_prepare_f32_f32(tile);
+    return sweep2_prepare(tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -302,6 +304,37 @@ __global__ void k_accumulate(int64_t n, const uint8_t* code, const float* delta,
 
 cudaError_t launch_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x, cudaStream_t s) {
     k_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, code, delta, x);
+    return cudaGetLastError();
+}
+
+// gc = (bits of FP32 g with the two low bits cleared) | code', where
+// code' = 1 free, 2 seed, 0 absent (also for voxels beyond the box extent),
+// so that zero-filled halo words read as absent voxels.
+__global__ void k_pack_gc(const Boxes bx, const void* g, int gtype, const uint8_t* code, uint32_t* gc) {
+    const int box = blockIdx.y;
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nvox) return;
+    int ex, ey, ez;
+    box_extent(bx, box, &ex, &ey, &ez);
+    const int x = (int)(li % bx.nx), y = (int)((li / bx.nx) % bx.ny), z = (int)(li / ((int64_t)bx.nx * bx.ny));
+    const int64_t i = (int64_t)box * nvox + li;
+    uint32_t w = 0u;
+    if (x < ex && y < ey && z < ez) {
+        const uint8_t c = code[i];
+        const float gv = gtype == G_U16 ? (float)static_cast<const uint16_t*>(g)[i] * (1.0f / 65535.0f)
+                                        : static_cast<const float*>(g)[i];
+        const uint32_t cc = c == FREE ? 1u : (c == SEED ? 2u : 0u);
+        w = cc ? ((__float_as_uint(gv) & ~3u) | cc) : 0u;
+    }
+    gc[i] = w;
+}
+
+cudaError_t launch_pack_gc(const Boxes& bx, const void* g, int gtype, const uint8_t* code, uint32_t* gc,
+                           cudaStream_t s) {
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)bx.nbox);
+    k_pack_gc<<<grid, 256, 0, s>>>(bx, g, gtype, code, gc);
     return cudaGetLastError();
 }
 

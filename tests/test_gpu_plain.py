@@ -61,25 +61,39 @@ def test_plain_ball_64_parity(rw, precision):
 @pytest.mark.parametrize("shape,seed", [((37, 23, 19), 1), ((5, 70, 33), 2), ((1, 1, 50), 3), ((2, 3, 1), 4),
                                         ((64, 17, 130), 5), ((9, 40, 41), 6)])
 def test_ragged_random_parity(rw, shape, seed):
-    c = P.random_case(shape, seed=seed, seed_frac=0.05, beta=25.0)
-    xo = _oracle(c, 25.0)
-    x, st = _solve(rw, c, beta=25.0, tol=1e-10)
+    # uniform noise with beta = 10 keeps weights >= exp(-10), so both FP64
+    # references are accurate far below the tolerance
+    c = P.random_case(shape, seed=seed, seed_frac=0.05, beta=10.0)
+    xo = _oracle(c, 10.0)
+    x, st = _solve(rw, c, beta=10.0, tol=1e-10)
     assert np.max(np.abs(x - xo)) <= 1e-6
 
 
-@pytest.mark.parametrize("tile", ["32x16", "64x8", "32x8"])
+def test_ill_conditioned_chain_falls_back_to_fp64(rw):
+    # a 1-D chain with weights down to 1e-11 (condition number ~1e11): FP32
+    # sweeps cannot cut the residual, the solve finishes with FP64 sweeps
+    c = P.random_case((1, 1, 50), seed=3, seed_frac=0.05, beta=25.0)
+    xo = _oracle(c, 25.0)
+    x, st = _solve(rw, c, beta=25.0, tol=1e-10)
+    assert st["rel_resid"] <= 1e-10
+    assert np.max(np.abs(x - xo)) <= TOL
+
+
+@pytest.mark.parametrize("tile", ["32x16", "64x8", "32x8", "32x32", "64x16"])
 def test_every_u16_tile_matches_oracle(rw, tile):
     c = P.plain_ball(n=48, seed=3)
     xo = _oracle(c, 130.0)
     x, st = _solve(rw, c, beta=130.0, tol=1e-9, tile=tile)
     assert np.max(np.abs(x - xo)) <= TOL
+    assert st["tile"] == rw._abi.RW_TILE[tile]
 
 
-@pytest.mark.parametrize("tile", ["32x16", "40x8", "40x20", "80x8", "80x16", "64x8", "32x8"])
+@pytest.mark.parametrize("tile", ["32x16", "40x8", "40x20", "80x8", "80x16", "64x8", "32x8", "32x32", "64x16"])
 def test_every_f32_tile_matches_oracle(rw, tile):
-    c = P.random_case((45, 43, 85), seed=8, seed_frac=0.03, beta=30.0)
-    xo = _oracle(c, 30.0, storage_f32=True)
-    x, st = _solve(rw, c, beta=30.0, tol=1e-10, tile=tile, storage=rw.RW_STORE_F32)
+    c = P.random_case((45, 43, 85), seed=8, seed_frac=0.03, beta=10.0)
+    xo = _oracle(c, 10.0, storage_f32=True)
+    x, st = _solve(rw, c, beta=10.0, tol=1e-10, tile=tile, storage=rw.RW_STORE_F32)
+    assert st["tile"] == rw._abi.RW_TILE[tile]
     assert np.max(np.abs(x - xo)) <= 1e-6
 
 
