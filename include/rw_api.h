@@ -117,7 +117,9 @@ typedef struct rw_opts {
 } rw_opts;
 
 enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, RW_TILE_40x20 = 4,
-       RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7, RW_TILE_32x32 = 8, RW_TILE_64x16 = 9 };
+       RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7, RW_TILE_32x32 = 8, RW_TILE_64x16 = 9,
+       /* warp-row tiles (28 columns + halo = one warp per row; FP32 only) */
+       RW_TILE_W28x28 = 10, RW_TILE_W28x12 = 11, RW_TILE_W28x20 = 12, RW_TILE_W28x28_8W = 13 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */

@@ -200,7 +200,7 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     } else if (nx <= 96 && nx % 80 == 0) {
         c = {5, 6, 9};
     } else {
-        c = {1, 8, 9, 2, 7};
+        c = {10, 11, 12, 13, 7, 1};
     }
     std::vector<int> ok;
     for (int t : c)
@@ -277,6 +277,7 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, v
         sa.p_in = p[par];
         sa.u_out = u[par ^ 1];
         sa.p_out = p[par ^ 1];
+        sa.parity = par;
         cudaError_t e = launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream);
         if (e != cudaSuccess && le == cudaSuccess) le = e;
         par ^= 1;
@@ -333,6 +334,7 @@ rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* co
         sa.p_in = p[par];
         sa.u_out = u[par ^ 1];
         sa.p_out = p[par ^ 1];
+        sa.parity = par;
         CK(counted(launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream)));
         par ^= 1;
     }
@@ -384,11 +386,11 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
         }
     }
     RCK(make_cfg(fp64, P.gtype, tile, bx, w->sms, ipg, &ps->cfg));
-    size_t part_elems = (size_t)bx.nbox * ps->cfg.ntx * ps->cfg.nty * ps->cfg.nzc * 3;
+    size_t part_elems = (size_t)bx.nbox * ps->cfg.ntx * ps->cfg.nty * ps->cfg.nzc * 6;
     for (int t : ps->cands) {
         SweepCfg c2;
         RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2));
-        part_elems = std::max(part_elems, (size_t)bx.nbox * c2.ntx * c2.nty * c2.nzc * 3);
+        part_elems = std::max(part_elems, (size_t)bx.nbox * c2.ntx * c2.nty * c2.nzc * 6);
     }
     RCK(ws_get_t(w, S_PART, part_elems * sizeof(double), part));
     return RW_OK;
@@ -459,6 +461,9 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     ra.x = P.x_hi;
     ra.u = ps.u[0];
     ra.p = ps.p[0];
+    ra.p_other = ps.p[1];
+    ra.sc = sc;
+    ra.keep_p = 0;
     ra.part = rpart;
     ra.blocks_per_box = bpb;
     ra.mbeta = -(double)o.beta;
@@ -494,10 +499,12 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     std::vector<BoxScalars> h(bx.nbox);
     std::vector<double> prev(bx.nbox, -1.0);
     const double t0 = now_ms();
+    int restart = 1;
     for (int r = 0; r < max_rounds; ++r) {
         const double eps_inner = cur64 ? 0.0 : 1e-5;
         CK(cudaMemsetAsync(nact, 0, sizeof(int), w->stream));
-        CK(counted(launch_start_round(sc, bx.nbox, r, o.tol, eps_inner, o.max_iter, nact, w->stream)));
+        CK(counted(launch_start_round(sc, bx.nbox, r, o.tol, eps_inner, o.max_iter, restart, nact, w->stream)));
+        restart = 0;
         CK(cudaMemcpyAsync(h.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaMemcpyAsync(w->pinned, nact, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaStreamSynchronize(w->stream));
@@ -512,7 +519,10 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
         sa.zc = ps.cfg.zc;
         const int64_t cap = R->sweeps + (int64_t)o.max_iter + 4 * ps.cfg.ipg;
         RCK(run_graph_chunks(w, ps.cfg, sa, ps.u, ps.p, cur64, P.gtype, nact, &R->sweeps, cap, &R->ms_sweeps));
+        // residual replacement: x_hi absorbs the FP32 correction, the FP64
+        // residual replaces the recursive one and the search direction is kept
         if (!cur64) CK(counted(launch_accumulate(ntot, P.code, delta, P.x_hi, w->stream)));
+        ra.keep_p = 1;
         CK(counted(launch_residual(cur64, ra, delta, w->stream)));
         CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
         if (!cur64) {
@@ -521,7 +531,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
             bool stagnated = false;
             for (int b = 0; b < bx.nbox; ++b) {
                 const BoxScalars& S = h[b];
-                if (S.nseed == 0 || S.nfree == 0 || !(S.bb > 0.0)) continue;
+                if (S.nseed == 0 || S.nfree == 0 || !(S.bb > 0.0) || S.status == 5) continue;
                 if (S.rr_true > o.tol * o.tol * S.bb && prev[b] > 0.0 && S.rr_true > 1e-2 * prev[b]) stagnated = true;
             }
             if (stagnated) {
@@ -530,7 +540,10 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
                 RCK(prec_setup(w, P, o, 1, &ps, &part));
                 ra.u = ps.u[0];
                 ra.p = ps.p[0];
+                ra.p_other = ps.p[1];
+                ra.keep_p = 0;
                 sa.x = P.x_hi;
+                restart = 1;
                 CK(counted(launch_residual(1, ra, nullptr, w->stream)));
                 CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
                 max_rounds = r + 2;

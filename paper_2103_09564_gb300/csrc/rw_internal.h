@@ -18,14 +18,17 @@ struct BoxScalars {
     double tol2;     // the round stops when rr <= tol2
     double rr_true;  // FP64 ||b - A x||^2 of the last residual sweep
     double dbeta;    // adjoint: dl/dbeta
+    double alpha_keep;  // alpha_k kept across a residual replacement (phase 2)
     int iters;       // regular sweeps completed (all rounds)
     int max_iter;
     int active;      // 1 while the box iterates
-    int phase;       // 0: next sweep is the initial (alpha = beta = 0) sweep
+    int phase;       // next sweep: 0 restart (p = u), 1 regular, 2 inner products of a replaced residual
+    int par;         // buffer (0/1) holding the system's latest u and p
     int nseed;
     int nfree;
     unsigned counter;  // arrival counter of the last-block reduction
-    int status;      // 0 ok, 3 not converged, 2 no seeds
+    int status;      // 0 ok, 5 breakdown (restart next round)
+    int pad;
 };
 
 // A batch of equally padded boxes: box b covers [0,nx) x [0,ny) x [0,nz) in
@@ -50,6 +53,7 @@ struct SweepArgs {
     BoxScalars* sc;
     double* partials;       // [nbox][tiles][3]
     int* n_active;
+    int parity;             // index of the (u, p) buffers this launch reads
     float c2f;              // -beta * log2(e), FP32 weights
     float wminf;
     double mbeta;           // -beta, FP64 weights
@@ -58,8 +62,9 @@ struct SweepArgs {
 
 enum GType { G_U16 = 0, G_F32 = 1 };
 enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE_80x8 = 5, TILE_80x16 = 6,
-              TILE_32x8 = 7, TILE_32x32 = 8, TILE_64x16 = 9 };
-constexpr int N_TILES = 10;
+              TILE_32x8 = 7, TILE_32x32 = 8, TILE_64x16 = 9, TILE_W28x28 = 10, TILE_W28x12 = 11, TILE_W28x20 = 12,
+              TILE_W28x28_8W = 13 };
+constexpr int N_TILES = 14;
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
 // combination that is not instantiated.
@@ -80,8 +85,11 @@ struct ResidArgs {
     const float* x0;       // initial guess (nullable)
     const float* rhs;      // extra right-hand side on free voxels (nullable)
     void* x;               // FP64 solution x_hi
-    void* u;               // out: u_0 = r / d  (T)
-    void* p;               // out: zeroed       (T)
+    void* u;               // out: u = D^-1 r  (T), buffer 0
+    void* p;               // p buffer 0 (T): zeroed, or kept (keep_p)
+    void* p_other;         // p buffer 1 (T): source when a system's latest p is there
+    const BoxScalars* sc;  // for keep_p: which buffer holds each system's p
+    int keep_p;            // 1: residual replacement keeps the search direction
     double* part;          // [nbox][blocks][4]: bb, rr, nseed, nfree
     int blocks_per_box;
     double mbeta, wmin;
@@ -93,7 +101,7 @@ cudaError_t launch_accumulate(int64_t n, const uint8_t* code, const float* delta
 cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, BoxScalars* sc, int first,
                               cudaStream_t s);
 cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
-                               int* n_active, cudaStream_t s);
+                               int restart, int* n_active, cudaStream_t s);
 cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, const BoxScalars* sc, void* x,
                               cudaStream_t s);
 cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s);

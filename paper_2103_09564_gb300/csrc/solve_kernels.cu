@@ -15,6 +15,10 @@ cudaError_t sweep2_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s
 cudaError_t sweep2_prepare(int tile);
 int sweep2_occupancy(int tile);
 size_t sweep2_smem(int tile);
+cudaError_t sweep3_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep3_prepare(int tile);
+int sweep3_occupancy(int tile);
+size_t sweep3_smem(int tile);
 cudaError_t sweep_launch_d64_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_launch_d64_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_prepare_d64_u16(int tile);
@@ -44,21 +48,21 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
         return 0;
     }
     if (fp64) slot = gtype == G_U16 ? sweep_occupancy_d64_u16(tile) : sweep_occupancy_d64_f32(tile);
-    else slot = sweep2_occupancy(tile);
+    else slot = tile >= TILE_W28x28 ? sweep3_occupancy(tile) : sweep2_occupancy(tile);
     return slot;
 }
 
 
 void tile_dims(int tile, int* tx, int* ty) {
-    static const int T[N_TILES][2] = {{0, 0}, {32, 16}, {64, 8}, {40, 8}, {40, 20}, {80, 8}, {80, 16}, {32, 8},
-                                      {32, 32}, {64, 16}};
+    static const int T[N_TILES][2] = {{0, 0},   {32, 16}, {64, 8},  {40, 8},  {40, 20}, {80, 8}, {80, 16},
+                                      {32, 8},  {32, 32}, {64, 16}, {28, 28}, {28, 12}, {28, 20}, {28, 28}};
     if (tile < 1 || tile >= N_TILES) tile = 1;
     *tx = T[tile][0];
     *ty = T[tile][1];
 }
 
 int sweep_threads(int tile) {
-    static const int N[N_TILES] = {0, 512, 512, 320, 800, 640, 640, 256, 1024, 1024};
+    static const int N[N_TILES] = {0, 512, 512, 320, 800, 640, 640, 256, 1024, 1024, 512, 256, 256, 256};
     return (tile >= 1 && tile < N_TILES) ? N[tile] : 0;
 }
 
@@ -68,17 +72,18 @@ size_t sweep_smem_bytes(int fp64, int tile) {
     int tx, ty;
     tile_dims(tile, &tx, &ty);
     const int r2 = (tx + 4) * (ty + 4);
-    return fp64 ? (size_t)sweep_planes_bytes<double>(r2) : sweep2_smem(tile);
+    if (fp64) return (size_t)sweep_planes_bytes<double>(r2);
+    return tile >= TILE_W28x28 ? sweep3_smem(tile) : sweep2_smem(tile);
 }
 
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     if (fp64) return gtype == G_U16 ? sweep_launch_d64_u16(tile, a, grid, s) : sweep_launch_d64_f32(tile, a, grid, s);
-    return sweep2_launch(tile, a, grid, s);
+    return tile >= TILE_W28x28 ? sweep3_launch(tile, a, grid, s) : sweep2_launch(tile, a, grid, s);
 }
 
 cudaError_t sweep_prepare(int fp64, int gtype, int tile) {
     if (fp64) return gtype == G_U16 ? sweep_prepare_d64_u16(tile) : sweep_prepare_d64_f32(tile);
-    return sweep2_prepare(tile);
+    return tile >= TILE_W28x28 ? sweep3_prepare(tile) : sweep2_prepare(tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,7 +174,8 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
             }
         }
         static_cast<T*>(a.u)[i] = uo;
-        static_cast<T*>(a.p)[i] = (T)0;
+        if (!a.keep_p) static_cast<T*>(a.p)[i] = (T)0;
+        else if (a.sc[box].par == 1) static_cast<T*>(a.p)[i] = static_cast<const T*>(a.p_other)[i];
         if (delta) delta[i] = 0.0f;
     }
     __shared__ double red[4][8];
@@ -243,7 +249,7 @@ cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, 
 // Decide which systems iterate in this round and set their inner target:
 // stop the round at ||r|| <= max(tol ||b||, eps_inner ||r_round_start||).
 __global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
-                              int* n_active) {
+                              int restart, int* n_active) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
     BoxScalars* S = sc + b;
@@ -259,7 +265,15 @@ __global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, d
     S->counter = 0u;
     if (need) {
         S->active = 1;
-        S->phase = 0;
+        // continue the Krylov process across the residual replacement when
+        // possible (reliable update); restart on the first round, after a
+        // precision switch, or after a breakdown
+        if (restart || round == 0 || S->status == 5 || !(S->gam > 0.0)) {
+            S->phase = 0;
+            S->status = 0;
+        } else {
+            S->phase = 2;
+        }
         S->alpha = 0.0;
         S->beta = 0.0;
         S->tol2 = fmax(tgt, eps_inner * eps_inner * S->rr_true);
@@ -270,8 +284,8 @@ __global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, d
 }
 
 cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
-                               int* n_active, cudaStream_t s) {
-    k_start_round<<<(nbox + 127) / 128, 128, 0, s>>>(sc, nbox, round, tol, eps_inner, max_iter, n_active);
+                               int restart, int* n_active, cudaStream_t s) {
+    k_start_round<<<(nbox + 127) / 128, 128, 0, s>>>(sc, nbox, round, tol, eps_inner, max_iter, restart, n_active);
     return cudaGetLastError();
 }
 

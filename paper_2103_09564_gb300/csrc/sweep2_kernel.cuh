@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
     float* sWz = sWy + 3 * R2;                                  // [3][R2] w(i-z, i)
     float* sUn = sWz + 3 * R2;                                  // [2][R2] u_k+1
     float* rX = sUn + 2 * R2;                                   // [NR][NI] x (delta)
-    __shared__ double red[3 * (NT / 32)];
+    __shared__ double red[6 * (NT / 32)];
     __shared__ int s_last;
 
     const int tid = threadIdx.x;
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
         if (!S->active) continue;
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
         const float alpha = (float)S->alpha, bcg = (float)S->beta;
+        const bool keep_p = S->phase == 2;
         int ex = nx, ey = ny, ez = nz;
         if (A.bx.ext) {
             ex = A.bx.ext[3 * box];
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
         }
         const int ox = tx * TX, oy = ty * TY, z0 = tz * A.zc;
         const int z1 = min(z0 + A.zc, ez);
-        float a_gam = 0.f, a_rr = 0.f, a_del = 0.f;
+        float a_gam = 0.f, a_rr = 0.f, a_del = 0.f, a_eps = 0.f, a_pi = 0.f, a_tau = 0.f;
         if (ox < ex && oy < ey && z0 < ez) {
             const int64_t base = (int64_t)box * bstride;
             // per-item element tables: A over R2, B over R1, C over the interior
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
                         if (!(f & 16)) continue;
                         const int e = tid + j * NT;
                         const uint32_t g0 = G[e];
-                        sP[f3 * R2 + e] = ((g0 & 3u) == 1u) ? U[e] + bcg * Pm[e] : 0.0f;
+                        sP[f3 * R2 + e] = keep_p ? Pm[e] : (((g0 & 3u) == 1u) ? U[e] + bcg * Pm[e] : 0.0f);
                         sWx[f3 * R2 + e] = (f & 2) ? w_of(g0, G[e + 1], c2, wmin) : 0.0f;
                         sWy[f3 * R2 + e] = (f & 4) ? w_of(g0, G[e + W2], c2, wmin) : 0.0f;
                         sWz[f3 * R2 + e] = (zedge && (f & 8)) ? w_of(Gp[e], g0, c2, wmin) : 0.0f;
@@ -240,14 +241,15 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
                         const int e = be[j];
                         if (e < 0) continue;
                         const float p0 = P[e];
-                        float un = 0.0f, d = 0.0f;
+                        float un = 0.0f, d = 0.0f, sv = 0.0f;
                         if ((G[e] & 3u) == 1u) {
                             const float wxm = Wx[e - 1], wxp = Wx[e], wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e],
                                         wzp = Wzh[e];
                             d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
                             const float nb = ((wxm * P[e - 1] + wxp * P[e + 1]) + (wym * P[e - W2] + wyp * P[e + W2])) +
                                              (wzm * Pl[e] + wzp * Ph[e]);
-                            if (d > 0.0f) un = U[e] - alpha * (d * p0 - nb) / d;
+                            sv = d * p0 - nb;
+                            if (d > 0.0f) un = U[e] - alpha * sv / d;
                         }
                         Un[e] = un;
                         if (out && bi[j] >= 0) {
@@ -259,6 +261,9 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
                                 const float du = d * un;
                                 a_gam += du * un;
                                 a_rr += du * du;
+                                a_eps += un * sv;
+                                a_pi += p0 * sv;
+                                a_tau += du * p0;
                             }
                         }
                     }
@@ -266,13 +271,12 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
             }
             cp_async_wait<0>();
         }
-        double v0 = (double)a_gam, v1 = (double)a_rr, v2 = (double)a_del;
-        block_reduce3<NT>(v0, v1, v2, red);
+        double v[6] = {(double)a_gam, (double)a_rr, (double)a_del, (double)a_eps, (double)a_pi, (double)a_tau};
+        block_reduce<NT, 6>(v, red);
         if (tid == 0) {
-            double* pp = A.partials + ((int64_t)box * tpb + t) * 3;
-            pp[0] = v0;
-            pp[1] = v1;
-            pp[2] = v2;
+            double* pp = A.partials + ((int64_t)box * tpb + t) * 6;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
             const unsigned prev = atomicAdd(&S->counter, 1u);
             s_last = (prev == (unsigned)tpb - 1u);
@@ -280,17 +284,15 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks<NT>()) k_sweep2(const Sw
         __syncthreads();
         if (s_last) {
             __threadfence();
-            double t0 = 0, t1 = 0, t2 = 0;
-            const double* pb = A.partials + (int64_t)box * tpb * 3;
-            for (int k = tid; k < tpb; k += NT) {
-                t0 += __ldcg(pb + 3 * k);
-                t1 += __ldcg(pb + 3 * k + 1);
-                t2 += __ldcg(pb + 3 * k + 2);
-            }
-            block_reduce3<NT>(t0, t1, t2, red);
+            double tv[6] = {0, 0, 0, 0, 0, 0};
+            const double* pb = A.partials + (int64_t)box * tpb * 6;
+            for (int k = tid; k < tpb; k += NT)
+#pragma unroll
+                for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);
+            block_reduce<NT, 6>(tv, red);
             if (tid == 0) {
                 S->counter = 0u;
-                finalize_box(S, t0, t1, t2, A.n_active);
+                finalize_box(S, tv, A.n_active, A.parity ^ 1);
             }
         }
         __syncthreads();

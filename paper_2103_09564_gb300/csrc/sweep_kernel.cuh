@@ -71,57 +71,67 @@ __device__ __forceinline__ T gval(const G* g, int64_t i) {
     }
 }
 
-template <int NT>
-__device__ __forceinline__ void block_reduce3(double& a, double& b, double& c, double* red) {
+// Block-wide FP64 sum of NV per-thread values (warp shuffles, then one warp);
+// the result is valid in thread 0.  red: NV * (NT / 32) doubles.
+template <int NT, int NV>
+__device__ __forceinline__ void block_reduce(double* v, double* red) {
     constexpr int NW = NT / 32;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
-    }
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[wid] = a;
-        red[NW + wid] = b;
-        red[2 * NW + wid] = c;
-    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k * NW + wid] = v[k];
     __syncthreads();
     if (wid == 0) {
-        a = lane < NW ? red[lane] : 0.0;
-        b = lane < NW ? red[NW + lane] : 0.0;
-        c = lane < NW ? red[2 * NW + lane] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
-            c += __shfl_down_sync(0xffffffffu, c, o);
-        }
+        for (int k = 0; k < NV; ++k) v[k] = lane < NW ? red[k * NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     }
     __syncthreads();
 }
 
 // Scalar recurrences of the system after its sweep (run by one thread of the
-// last CTA).  g = gamma_k+1, rr = ||r_k+1||^2, dl = delta_k+1.
-__device__ __forceinline__ void finalize_box(BoxScalars* S, double g, double rr, double dl, int* n_active) {
+// last CTA).  v = {gamma, ||r||^2, delta, eps, pi, tau} of the sweep that
+// produced u = u_k+1 from the direction p = p_k:
+//   gamma = (r, u), delta = (u, A u), eps = (u, A p), pi = (p, A p),
+//   tau = (r, p), with r = D u.
+// The next direction p' = u + beta p is made A-conjugate to p explicitly,
+// beta = -eps / pi, and the step is the exact line minimum along it,
+//   alpha = (r, p') / (p', A p') = (gamma + beta tau) / (delta + 2 beta eps + beta^2 pi).
+// In exact arithmetic these equal the classic PCG scalars; computing them from
+// the sweep's own inner products keeps them valid after the residual is
+// replaced by the FP64 one (the search direction survives the replacement).
+// out_par is the buffer index the sweep wrote.
+__device__ __forceinline__ void finalize_box(BoxScalars* S, const double* v, int* n_active, int out_par) {
+    const double g = v[0], rr = v[1], dl = v[2], ep = v[3], pi = v[4], tau = v[5];
     bool stop;
+    S->par = out_par;
+    S->rr = rr;
     if (S->phase == 0) {
-        // initial sweep (alpha = beta = 0): gamma_0, delta_0
+        // restart sweep (alpha = beta = 0, p = u): alpha_0 = gamma_0 / delta_0
         S->phase = 1;
-        S->rr = rr;
         S->gam = g;
         stop = !(rr > S->tol2) || !(g > 0.0) || !(dl > 0.0);
         S->alpha = stop ? 0.0 : g / dl;
         S->beta = 0.0;
     } else {
-        S->iters += 1;
-        S->rr = rr;
-        const double bcg = g / S->gam;
-        const double den = dl - bcg * g / S->alpha;
-        stop = !(rr > S->tol2) || S->iters >= S->max_iter || !(g > 0.0) || !(den > 0.0);
+        if (S->phase == 1) S->iters += 1;
+        S->phase = 1;
+        const double bcg = pi > 0.0 ? -ep / pi : 0.0;
+        const double den = dl + 2.0 * bcg * ep + bcg * bcg * pi;
+        const double num = g + bcg * tau;
+        const bool ok = pi > 0.0 && den > 0.0 && num > 0.0;
+        stop = !(rr > S->tol2) || S->iters >= S->max_iter || !ok;
+        if (!ok && rr > S->tol2) S->status = 5;
         if (!stop) {
             S->beta = bcg;
-            S->alpha = g / den;
+            S->alpha = num / den;
             S->gam = g;
         }
     }
@@ -150,7 +160,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
     T* sWy = sWx + 4 * R2;                    // [4][R2] weight (i, i+y)
     T* sWz = sWy + 4 * R2;                    // [4][R2] weight (i-z, i)
     uint8_t* sC = reinterpret_cast<uint8_t*>(sWz + 4 * R2);  // [2][R2] code
-    __shared__ double red[3 * (NT / 32)];
+    __shared__ double red[6 * (NT / 32)];
     __shared__ int s_last;
 
     const int tid = threadIdx.x;
@@ -173,6 +183,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
         if (!S->active) continue;  // same value for every thread of the CTA
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
         const T alpha = (T)S->alpha, bcg = (T)S->beta;
+        const bool keep_p = S->phase == 2;
         int ex = nx, ey = ny, ez = nz;
         if (A.bx.ext) {
             ex = A.bx.ext[3 * box];
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
         const int ox = tx * TX, oy = ty * TY, z0 = tz * A.zc;
         const int z1 = min(z0 + A.zc, ez);
         const int64_t base = (int64_t)box * bstride;
-        acc a_gam = 0, a_rr = 0, a_del = 0;
+        acc a_gam = 0, a_rr = 0, a_del = 0, a_eps = 0, a_pi = 0, a_tau = 0;
 
         if (ox < ex && oy < ey && z0 < ez) {
             for (int zf = z0 - 2; zf <= z1 + 1; ++zf) {
@@ -203,7 +214,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
                     sC[f2 * R2 + e] = c;
                     sG[f2 * R2 + e] = gv;
                     sUk[f2 * R2 + e] = uk;
-                    sP[f3 * R2 + e] = (c == FREE) ? uk + bcg * pm : (T)0;
+                    sP[f3 * R2 + e] = keep_p ? pm : ((c == FREE) ? uk + bcg * pm : (T)0);
                 }
                 __syncthreads();
                 // -- A2: forward edge weights of plane zf (and z-edges to zf-1)
@@ -240,15 +251,15 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
                         const int e = jy * W2 + jx;
                         const uint8_t c = sC[m2 * R2 + e];
                         const T p0 = P[e];
-                        T un = 0, d = 0;
+                        T un = 0, d = 0, sv = 0;
                         if (c == FREE) {
                             const T wxm = Wx[e - 1], wxp = Wx[e], wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e],
                                     wzp = Wzh[e];
                             d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
                             const T nb = ((wxm * P[e - 1] + wxp * P[e + 1]) + (wym * P[e - W2] + wyp * P[e + W2])) +
                                          (wzm * Pl[e] + wzp * Ph[e]);
-                            const T s = d * p0 - nb;
-                            if (d > (T)0) un = sUk[m2 * R2 + e] - alpha * s / d;
+                            sv = d * p0 - nb;
+                            if (d > (T)0) un = sUk[m2 * R2 + e] - alpha * sv / d;
                         }
                         sUn[m3 * R2 + e] = un;
                         if (zint && jx >= 2 && jx < TX + 2 && jy >= 2 && jy < TY + 2) {
@@ -262,6 +273,9 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
                                     const acc du = (acc)d * (acc)un;
                                     a_gam += du * (acc)un;
                                     a_rr += du * du;
+                                    a_eps += (acc)un * (acc)sv;
+                                    a_pi += (acc)p0 * (acc)sv;
+                                    a_tau += du * (acc)p0;
                                 }
                             }
                         }
@@ -296,13 +310,12 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
             }
         }
         // -- reductions: block (FP64), then the last CTA of the system
-        double v0 = (double)a_gam, v1 = (double)a_rr, v2 = (double)a_del;
-        block_reduce3<NT>(v0, v1, v2, red);
+        double v[6] = {(double)a_gam, (double)a_rr, (double)a_del, (double)a_eps, (double)a_pi, (double)a_tau};
+        block_reduce<NT, 6>(v, red);
         if (tid == 0) {
-            double* pp = A.partials + ((int64_t)box * tpb + t) * 3;
-            pp[0] = v0;
-            pp[1] = v1;
-            pp[2] = v2;
+            double* pp = A.partials + ((int64_t)box * tpb + t) * 6;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
             const unsigned prev = atomicAdd(&S->counter, 1u);
             s_last = (prev == (unsigned)tpb - 1u);
@@ -310,17 +323,15 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
         __syncthreads();
         if (s_last) {
             __threadfence();
-            double t0 = 0, t1 = 0, t2 = 0;
-            const double* pb = A.partials + (int64_t)box * tpb * 3;
-            for (int k = tid; k < tpb; k += NT) {
-                t0 += __ldcg(pb + 3 * k);
-                t1 += __ldcg(pb + 3 * k + 1);
-                t2 += __ldcg(pb + 3 * k + 2);
-            }
-            block_reduce3<NT>(t0, t1, t2, red);
+            double tv[6] = {0, 0, 0, 0, 0, 0};
+            const double* pb = A.partials + (int64_t)box * tpb * 6;
+            for (int k = tid; k < tpb; k += NT)
+#pragma unroll
+                for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);
+            block_reduce<NT, 6>(tv, red);
             if (tid == 0) {
                 S->counter = 0u;
-                finalize_box(S, t0, t1, t2, A.n_active);
+                finalize_box(S, tv, A.n_active, A.parity ^ 1);
             }
         }
         __syncthreads();

@@ -8,6 +8,9 @@ import phantoms as P
 from oracle import hrw
 
 pytestmark = pytest.mark.gpu
+# Brick systems can hold weakly coupled pockets (isolated eigenvalues of the
+# Jacobi-scaled matrix near 1e-6): there a relative residual of 1e-9 still
+# allows 1e-3 of error, so the parity runs solve every brick to 1e-11.
 TOL = 1e-4
 NEAR = 1e-4      # a pruning decision may differ only this close to its threshold
 
@@ -89,7 +92,7 @@ def test_full_run_parity(rw, n, s, seed):
     else:
         ph = P.vessel_tree(n=n, seed=seed, n_segments=30)
     pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
-    opts = rw.Opts(brick_size=s, beta=130.0, tol=1e-9)
+    opts = rw.Opts(brick_size=s, beta=130.0, tol=1e-11)
     tree = rw.Tree(pyr, opts)
     st = tree.run(ph["labels_xyz"], ph["labels_value"])
     q = O.quantize(ph["volume"], 0.0, 5000.0, True)
@@ -118,9 +121,9 @@ def test_single_brick_equals_plain(rw):
 def test_no_pruning_parity_and_agreement(rw):
     ph = P.vessel_tree(n=64, seed=6, n_segments=30)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    t1 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9, prune_hom=0, prune_dt=0))
+    t1 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11, prune_hom=0, prune_dt=0))
     t1.run(ph["labels_xyz"], ph["labels_value"])
-    t2 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9))
+    t2 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11))
     s2 = t2.run(ph["labels_xyz"], ph["labels_value"])
     a, b = t1.read_level(pyr.levels - 1), t2.read_level(pyr.levels - 1)
     assert s2["bricks_pruned"] > 0
@@ -137,7 +140,7 @@ def test_incremental_update_parity(rw):
     ph = P.vessel_tree(n=64, seed=7, n_segments=30)
     n0 = len(ph["labels_value"]) - 6
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-9)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-11)
     tree = rw.Tree(pyr, opts)
     tree.run(ph["labels_xyz"][:n0], ph["labels_value"][:n0])
     su = tree.update_seeds(ph["labels_xyz"][n0:], ph["labels_value"][n0:])
@@ -155,7 +158,7 @@ def test_incremental_update_parity(rw):
 def test_update_without_labels_keeps_everything(rw):
     ph = P.vessel_tree(n=32, seed=3, n_segments=10)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9))
+    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11))
     tree.run(ph["labels_xyz"], ph["labels_value"])
     before = tree.read_level(pyr.levels - 1).copy()
     su = tree.update_seeds(np.zeros((0, 3)), np.zeros(0))
@@ -166,8 +169,8 @@ def test_update_without_labels_keeps_everything(rw):
 def test_per_brick_sequential_equals_batched(rw):
     ph = P.vessel_tree(n=64, seed=8, n_segments=20)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    a = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9))
+    a = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11))
     a.run(ph["labels_xyz"], ph["labels_value"])
-    b = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9, batch_bricks=0, precision="fp64"))
+    b = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11, batch_bricks=0, precision="fp64"))
     b.run(ph["labels_xyz"], ph["labels_value"])
     assert np.max(np.abs(a.read_level(pyr.levels - 1) - b.read_level(pyr.levels - 1))) <= TOL
