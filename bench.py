@@ -172,7 +172,7 @@ def run(args):
     code = torch.from_numpy(c["code"]).to(dev)
     val = torch.from_numpy(c["value"]).to(dev)
     out = torch.empty_like(vol)
-    opts = rw.Opts(beta=BETA, tol=TOL)
+    opts = rw.Opts(beta=BETA, tol=TOL, tile=args.tile)
 
     def step():
         _, st = rw.rw_solve(vol, code, val, opts, out=out)
@@ -265,6 +265,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--tile", default="auto", help="sweep tile (default: autotuned)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
