@@ -146,6 +146,10 @@ typedef struct rw_stats {
 typedef struct rw_pyramid rw_pyramid;
 typedef struct rw_tree rw_tree;
 
+/* Limits of rw_solve_noalloc (its scratch is a fixed device array). */
+#define RW_NOALLOC_MAX_VOXELS 262144  /* voxels over the whole batch (64^3) */
+#define RW_NOALLOC_MAX_BATCH 64
+
 void rw_opts_default(rw_opts* opts);
 const char* rw_last_error(void);
 const char* rw_version(void);
@@ -161,6 +165,32 @@ rw_status rw_release_workspace(void);
  * a volume has no seed.  A volume whose right-hand side is 0 gets x_U = 0. */
 rw_status rw_solve(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opts* opts,
                    const float* x0, float* x_out, rw_stats* stats, void* stream);
+
+/* rw_solve for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the plain solve above.
+ * Some callers must not call cudaMalloc/cudaFree while they run — an
+ * interactive labelling loop with a latency budget (both calls can
+ * synchronise the whole device), a plug-in inside a host application that
+ * owns the GPU memory budget, a service that fixes its footprint at start-up.
+ * This entry point allocates nothing: its scratch is one file-scope device
+ * array of about 10.5 MB that every GPU loading the library keeps until the
+ * process exits.  Same arguments and results as rw_solve, with these
+ * differences:
+ *  - every array must be device memory (no host staging);
+ *  - at most RW_NOALLOC_MAX_VOXELS voxels in total and RW_NOALLOC_MAX_BATCH
+ *    volumes; larger inputs are rejected with RW_ERR_INVALID_ARG;
+ *  - opts->precision must be RW_MIXED and vol->storage RW_STORE_UNORM16; a
+ *    system that FP32 sweeps cannot resolve returns RW_ERR_NOT_CONVERGED
+ *    (rw_solve would finish it with FP64 sweeps);
+ *  - work runs on `stream` itself (no internal stream, CUDA graph or timing
+ *    event) and the stream is synchronised before returning.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any
+ * stream capture.  All calls share the array and each call clears what must
+ * start at zero: calls that overlap on the GPU (from several streams or
+ * threads) race and must be serialised by the caller. */
+rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opts* opts,
+                           const float* x0, float* x_out, rw_stats* stats, void* stream);
 
 /* Adjoint of rw_solve (not in the paper; gradient of a loss l(x)): solves
  * L_U lambda = (dl/dx)_U with the same PCG (L_U is symmetric) and returns

@@ -22,7 +22,7 @@ from ._abi import (RW_CODE_ABSENT, RW_CODE_FREE, RW_CODE_SEED, RW_FP64, RW_MIXED
                    RW_NODE_CFL_ADDED, RW_NODE_DT, RW_NODE_HOM, RW_NODE_NO_SEEDS, RW_NODE_PRUNABLE, RW_NODE_REUSED,
                    RW_NODE_SIMILAR, RW_NODE_SOLVED, RW_STORE_F32, RW_STORE_UNORM16, LibraryMissing)
 
-__all__ = ["RWError", "Opts", "rw_solve", "rw_solve_adjoint", "rw_build_pyramid", "Pyramid", "Tree", "load",
+__all__ = ["RWError", "Opts", "rw_solve", "rw_solve_noalloc", "rw_solve_adjoint", "rw_build_pyramid", "Pyramid", "Tree", "load",
            "release_workspace", "version"]
 
 
@@ -152,6 +152,34 @@ def rw_solve(volume, code, value=None, opts=None, x0=None, out=None, *, lo=0.0, 
     rc = load().rw_solve(ctypes.byref(v), ctypes.byref(sm), ctypes.byref(opts), xi.ptr, o.ptr, ctypes.byref(st),
                          _stream(va, c, val, xi, o))
     _check(rc, allow=(_abi.RW_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    d = st.as_dict()
+    d["status"] = rc
+    return o.obj, d
+
+
+def rw_solve_noalloc(volume, code, value=None, opts=None, x0=None, out=None, *, lo=0.0, hi=1.0, normalize=False,
+                     stream=None):
+    """rw_solve for callers that cannot allocate device memory: every array
+    must already live on the GPU (CUDA tensors, `out` included when given),
+    the scratch is the library's fixed device array (at most
+    RW_NOALLOC_MAX_VOXELS voxels).  Runs on `stream` (default: the current
+    torch stream).  Returns (x, stats)."""
+    torch = _torch()
+    batch = len(volume.shape) == 4
+    v, va, shp = _volume(volume, lo, hi, normalize, RW_STORE_UNORM16, batch)
+    c = _Arr(code, np.uint8)
+    val = _Arr(value, np.float32)
+    xi = _Arr(x0, np.float32)
+    if out is None:
+        out = torch.empty(tuple(volume.shape), dtype=torch.float32, device=volume.device)
+    o = _Arr(out)
+    sm = _abi.rw_seed_mask(c.ptr, val.ptr)
+    st = _abi.rw_stats()
+    opts = opts if opts is not None else Opts()
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    rc = load().rw_solve_noalloc(ctypes.byref(v), ctypes.byref(sm), ctypes.byref(opts), xi.ptr, o.ptr,
+                                 ctypes.byref(st), s)
+    _check(rc)
     d = st.as_dict()
     d["status"] = rc
     return o.obj, d

@@ -599,6 +599,9 @@ void stats_from(const SolveResult& R, const rw_opts& o, rw_stats* st, int* n_unc
 
 }  // namespace
 
+// Error text for the other translation units of the library.
+void rw_internal_set_error(const char* msg) { g_err = msg; }
+
 // ===========================================================================
 extern "C" {
 
