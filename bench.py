@@ -257,6 +257,141 @@ def run(args):
     return 0
 
 
+def _labels_np(ph):
+    return np.asarray(ph["labels_xyz"], dtype=np.float64), np.asarray(ph["labels_value"], dtype=np.float32)
+
+
+def run_hier(args):
+    """Hierarchical random walker on the vessel-tree phantom (n^3 uint16,
+    window [0, 5000]): one step = a full top-down run of all levels
+    (batched brick solves with pruning).  Beside it, the leaf level of a
+    256^3 phantom is solved twice from the same parent levels: batched FP32
+    sweeps (the default) and the per-brick FP64 solve, one brick per launch."""
+    import torch
+    import paper_2103_09564_gb300 as rw
+    import phantoms as P
+    n = int(os.environ.get("RW_BENCH_N", "1024"))
+    s = args.brick
+    dev = torch.device("cuda", 0)
+    ph = P.vessel_tree(n=n, seed=0, device=dev)
+    xyz, val = _labels_np(ph)
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    del ph
+    opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol)
+    tree = rw.Tree(pyr, opts)
+    for _ in range(max(3, args.warmup)):
+        tree.run(xyz, val)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            stats.append(tree.run(xyz, val))
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    vi = sum(st["voxel_iters"] for st in stats)
+    sweep_ms = sum(st["ms_sweeps"] for st in stats)
+    per_level = []
+    for k in range(pyr.levels):
+        fl, mn, mx, md = tree.node_stats(k)
+        per_level.append({"level": k, "dims": pyr.dims[k], "solved": int(np.count_nonzero(fl & rw.RW_NODE_SOLVED)),
+                          "prunable": int(np.count_nonzero(fl & rw.RW_NODE_PRUNABLE)),
+                          "conflict": int(np.count_nonzero(fl & rw.RW_NODE_CFL))})
+    # batched mixed vs per-brick FP64 on the leaf level of a 256^3 phantom
+    cmp = _compare_batched_vs_fp64(rw, P, s, args.tol)
+    peak, src = _peaks()
+    eff = 28.0 * vi / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+    line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"hierarchical random walker, {n}^3 uint16 vessel tree (phantoms.vessel_tree, "
+                                   f"seed 0, 200 segments), brick {s}, e 1.25, pruning hom+dt, tol {args.tol}",
+                       "levels": per_level, "bricks_solved_per_run": stats[0]["bricks_solved"],
+                       "bricks_pruned_per_run": stats[0]["bricks_pruned"], "labels": int(len(val))},
+            "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s",
+                         "frac": (eff / peak) if eff else None, "traffic": None,
+                         "kernel": "fused PCG sweep over the brick batches",
+                         "basis": "28 B per free-voxel iteration / device time of the sweeps", "peak_source": src},
+            "batched_vs_per_brick_fp64": cmp, "gpu_launches": int(sum(st["launches"] for st in stats)),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _compare_batched_vs_fp64(rw, P, s, tol):
+    ph = P.vessel_tree(n=256, seed=1, n_segments=60)
+    xyz, val = _labels_np(ph)
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    res = {}
+    leaf = {}
+    for name, kw in (("batched_mixed", {}), ("per_brick_fp64", {"batch_bricks": 0, "precision": "fp64"})):
+        t = rw.Tree(pyr, rw.Opts(brick_size=s, beta=BETA, tol=tol, **kw))
+        t.run(xyz, val)                       # warm-up (and autotuning)
+        st = None
+        for k in range(pyr.levels):
+            st = t.refine_level(k, xyz if k == 0 else None, val if k == 0 else None)
+        res[name] = {"leaf_voxel_iters": st["voxel_iters"], "leaf_ms": st["ms"], "leaf_bricks": st["bricks_solved"],
+                     "voxel_iter_per_s": st["voxel_iters"] / (st["ms"] / 1e3) if st["ms"] > 0 else None}
+        leaf[name] = t.read_level(pyr.levels - 1)
+    a, b = res["batched_mixed"]["voxel_iter_per_s"], res["per_brick_fp64"]["voxel_iter_per_s"]
+    res["speedup"] = (a / b) if a and b else None
+    res["max_abs_diff_leaf"] = float(np.max(np.abs(leaf["batched_mixed"] - leaf["per_brick_fp64"])))
+    res["workload"] = f"leaf level of the 256^3 vessel phantom (seed 1), brick {s}"
+    return res
+
+
+def run_adjoint(args):
+    """Differentiable solve on a batch of 32 volumes of 96^3 (balls / random
+    ellipsoids): one step = forward solve + adjoint solve + gradient kernel."""
+    import torch
+    import paper_2103_09564_gb300 as rw
+    import phantoms as P
+    n = int(os.environ.get("RW_BENCH_N", "96"))
+    b = P.adjoint_batch(n=n, batch=32)
+    dev = torch.device("cuda", 0)
+    g = torch.from_numpy(b["volume"]).to(dev)
+    code = torch.from_numpy(b["code"]).to(dev)
+    val = torch.from_numpy(b["value"]).to(dev)
+    y = torch.from_numpy(b["mask"].astype(np.float32)).to(dev)
+    opts = rw.Opts(beta=BETA, tol=args.tol)
+
+    def step():
+        x, s1 = rw.rw_solve(g, code, val, opts, storage=rw.RW_STORE_F32)
+        inter = (x * y).sum(dim=(1, 2, 3))
+        ssum = x.sum(dim=(1, 2, 3)) + y.sum(dim=(1, 2, 3))
+        num = 2 * inter + 1e-6
+        den = ssum + 1e-6
+        dl = ((num[:, None, None, None] - 2 * y * den[:, None, None, None]) /
+              (den[:, None, None, None] ** 2)) / x.shape[0]
+        dg, db, s2 = rw.rw_solve_adjoint(g, code, x, dl.contiguous(), opts)
+        return s1, s2
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = []
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            st.append(step())
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    vi = sum(a["voxel_iters"] + c["voxel_iters"] for a, c in st)
+    line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"differentiable random walker, 32 x {n}^3 (phantoms.adjoint_batch), forward + "
+                                   f"adjoint per step, soft-Dice loss, tol {args.tol}",
+                       "forward_iters": st[0][0]["iters"], "adjoint_iters": st[0][1]["iters"]},
+            "gpu_launches": int(sum(a["launches"] + c["launches"] for a, c in st)), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,9 +401,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", default="auto", help="sweep tile (default: autotuned)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "hier", "adjoint"],
+                    help="plain: the 256^3 headline workload; hier: hierarchical 1024^3 vessel tree; "
+                         "adjoint: 32 x 96^3 differentiable batch")
+    ap.add_argument("--brick", type=int, default=32)
+    ap.add_argument("--tol", type=float, default=1e-10)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "hier":
+        return run_hier(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run(args)
 
 

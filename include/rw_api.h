@@ -119,7 +119,10 @@ typedef struct rw_opts {
 enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, RW_TILE_40x20 = 4,
        RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7, RW_TILE_32x32 = 8, RW_TILE_64x16 = 9,
        /* warp-row tiles (28 columns + halo = one warp per row; FP32 only) */
-       RW_TILE_W28x28 = 10, RW_TILE_W28x12 = 11, RW_TILE_W28x20 = 12, RW_TILE_W28x28_8W = 13 };
+       RW_TILE_W28x28 = 10, RW_TILE_W28x12 = 11, RW_TILE_W28x20 = 12, RW_TILE_W28x28_8W = 13,
+       /* padded-layout tiles (16-byte asynchronous row copies; FP32 only, the default family) */
+       RW_TILE_P32x12 = 14, RW_TILE_P32x12_DEEP = 15, RW_TILE_P32x28 = 16, RW_TILE_P40x20 = 17,
+       RW_TILE_P40x8 = 18, RW_TILE_P32x20 = 19 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */

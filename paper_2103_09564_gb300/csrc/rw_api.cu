@@ -191,16 +191,19 @@ struct SweepCfg {
 std::map<std::string, std::pair<int, int>> g_tuned;  // class -> (tile, iters per graph)
 
 std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
+    // one list holds tiles of one layout family only (the autotuner times
+    // them on the same live vectors): padded k_sweep4 tiles, or the unpadded
+    // k_sweep2 tile for boxes narrower than one padded tile
     std::vector<int> c;
     (void)gtype;
     if (fp64) {
         c = {7, 3};
-    } else if (nx <= 48) {
-        c = {3, 4, 7};
-    } else if (nx <= 96 && nx % 80 == 0) {
-        c = {5, 6, 9};
+    } else if (nx <= 24) {
+        c = {7};
+    } else if (nx <= 48 || (nx % 40 == 0 && nx <= 160)) {
+        c = {17, 18};
     } else {
-        c = {10, 11, 12, 13, 7, 1};
+        c = {14, 15, 19, 16};
     }
     std::vector<int> ok;
     for (int t : c)
@@ -350,6 +353,8 @@ rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* co
 // (autotuned once per problem class), partial-sum storage.
 struct PrecState {
     int fp64 = 0;
+    Pad pad = {0, 0, 0};   // layout of u, p, delta, g|code for this precision
+    int64_t nvec = 0;      // elements of each streamed vector
     void* u[2] = {nullptr, nullptr};
     void* p[2] = {nullptr, nullptr};
     SweepCfg cfg;
@@ -364,17 +369,43 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     const int64_t ntot = (int64_t)bx.nx * bx.ny * bx.nz * bx.nbox;
     const size_t tsz = fp64 ? 8 : 4;
     ps->fp64 = fp64;
-    RCK(ws_get(w, S_U0, ntot * tsz, &ps->u[0]));
-    RCK(ws_get(w, S_U1, ntot * tsz, &ps->u[1]));
-    RCK(ws_get(w, S_P0, ntot * tsz, &ps->p[0]));
-    RCK(ws_get(w, S_P1, ntot * tsz, &ps->p[1]));
     ps->key = class_key(fp64, P.gtype, bx);
     ps->cands = tile_candidates(fp64, P.gtype, bx.nx);
     if (ps->cands.empty()) return fail(RW_ERR_INVALID_ARG, "no sweep kernel for this precision/storage");
+    if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0)
+        ps->cands = {o.tile};  // an explicit tile: its own layout, no tuning
+    ps->pad = {0, 0, 0};
+    ps->nvec = ntot;
+    if (!fp64 && ps->cands[0] >= TILE_PADDED_FIRST) {
+        // padded box: covers whole tiles of every candidate, 2-voxel margins
+        int px = 0, py = 0;
+        for (int t : ps->cands) {
+            int tx, ty;
+            tile_dims(t, &tx, &ty);
+            px = std::max(px, tx * ((bx.nx + tx - 1) / tx));
+            py = std::max(py, ty * ((bx.ny + ty - 1) / ty));
+        }
+        ps->pad.px = ((px + 4) + 3) & ~3;
+        ps->pad.py = py + 4;
+        ps->pad.pz = bx.nz + 4;
+        ps->nvec = (int64_t)ps->pad.px * ps->pad.py * ps->pad.pz * bx.nbox;
+    }
+    RCK(ws_get(w, S_U0, ps->nvec * tsz, &ps->u[0]));
+    RCK(ws_get(w, S_U1, ps->nvec * tsz, &ps->u[1]));
+    RCK(ws_get(w, S_P0, ps->nvec * tsz, &ps->p[0]));
+    RCK(ws_get(w, S_P1, ps->nvec * tsz, &ps->p[1]));
+    if (ps->pad.px) {
+        // the margins must read as absent voxels with zero vectors
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaMemsetAsync(ps->u[k], 0, ps->nvec * tsz, w->stream));
+            CK(cudaMemsetAsync(ps->p[k], 0, ps->nvec * tsz, w->stream));
+        }
+    }
     int tile = ps->cands[0];
     int ipg = std::max(2, o.iters_per_graph & ~1);
     ps->tune = false;
-    if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0) {
+    if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0 &&
+        std::find(ps->cands.begin(), ps->cands.end(), o.tile) != ps->cands.end()) {
         tile = o.tile;
     } else if (o.tile == RW_TILE_AUTO) {
         auto it = g_tuned.find(ps->key);
@@ -436,19 +467,21 @@ rw_status autotune(DevWorkspace* w, const SolveProblem& P, PrecState* ps, const 
 rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, SolveResult* R) {
     const Boxes& bx = P.bx;
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
-    const int64_t ntot = nvox * bx.nbox;
     int cur64 = o.precision == RW_FP64 ? 1 : 0;
     float* delta = nullptr;
     BoxScalars* sc = nullptr;
     int* nact = nullptr;
     double *rpart = nullptr, *part = nullptr;
-    if (!cur64) RCK(ws_get_t(w, S_DELTA, ntot * 4, &delta));
     RCK(ws_get_t(w, S_SC, bx.nbox * sizeof(BoxScalars), &sc));
     RCK(ws_get_t(w, S_NACT, 64, &nact));
     const int bpb = (int)((nvox + 255) / 256);
     RCK(ws_get_t(w, S_RPART, (size_t)bx.nbox * bpb * 4 * sizeof(double), &rpart));
     PrecState ps;
     RCK(prec_setup(w, P, o, cur64, &ps, &part));
+    if (!cur64) {
+        RCK(ws_get_t(w, S_DELTA, ps.nvec * 4, &delta));
+        if (ps.pad.px) CK(cudaMemsetAsync(delta, 0, ps.nvec * 4, w->stream));
+    }
 
     ResidArgs ra;
     ra.bx = bx;
@@ -464,6 +497,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     ra.p_other = ps.p[1];
     ra.sc = sc;
     ra.keep_p = 0;
+    ra.pad = ps.pad;
     ra.part = rpart;
     ra.blocks_per_box = bpb;
     ra.mbeta = -(double)o.beta;
@@ -471,8 +505,9 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
 
     uint32_t* gc = nullptr;
     if (!cur64) {
-        RCK(ws_get_t(w, S_GC, ntot * 4, &gc));
-        CK(counted(launch_pack_gc(bx, P.g, P.gtype, P.code, gc, w->stream)));
+        RCK(ws_get_t(w, S_GC, ps.nvec * 4, &gc));
+        if (ps.pad.px) CK(cudaMemsetAsync(gc, 0, ps.nvec * 4, w->stream));
+        CK(counted(launch_pack_gc(bx, ps.pad, P.g, P.gtype, P.code, gc, w->stream)));
     }
     CK(cudaMemsetAsync(sc, 0, bx.nbox * sizeof(BoxScalars), w->stream));
     if (P.init_x) CK(counted(launch_init_x(cur64, ra, w->stream)));
@@ -493,6 +528,9 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     sa.wminf = o.w_min;
     sa.mbeta = -(double)o.beta;
     sa.wmin = (double)o.w_min;
+    sa.px = ps.pad.px;
+    sa.py = ps.pad.py;
+    sa.pz = ps.pad.pz;
 
     const int mixed_rounds = std::max(1, o.refine_rounds);
     int max_rounds = cur64 ? 1 : mixed_rounds;
@@ -500,6 +538,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     std::vector<double> prev(bx.nbox, -1.0);
     const double t0 = now_ms();
     int restart = 1;
+    int fp64_restarts = 0;
     for (int r = 0; r < max_rounds; ++r) {
         const double eps_inner = cur64 ? 0.0 : 1e-5;
         CK(cudaMemsetAsync(nact, 0, sizeof(int), w->stream));
@@ -521,34 +560,42 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
         RCK(run_graph_chunks(w, ps.cfg, sa, ps.u, ps.p, cur64, P.gtype, nact, &R->sweeps, cap, &R->ms_sweeps));
         // residual replacement: x_hi absorbs the FP32 correction, the FP64
         // residual replaces the recursive one and the search direction is kept
-        if (!cur64) CK(counted(launch_accumulate(ntot, P.code, delta, P.x_hi, w->stream)));
+        if (!cur64) CK(counted(launch_accumulate(bx, ps.pad, P.code, delta, P.x_hi, w->stream)));
         ra.keep_p = 1;
         CK(counted(launch_residual(cur64, ra, delta, w->stream)));
         CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
-        if (!cur64) {
-            CK(cudaMemcpyAsync(h.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
-            CK(cudaStreamSynchronize(w->stream));
-            bool stagnated = false;
-            for (int b = 0; b < bx.nbox; ++b) {
-                const BoxScalars& S = h[b];
-                if (S.nseed == 0 || S.nfree == 0 || !(S.bb > 0.0) || S.status == 5) continue;
-                if (S.rr_true > o.tol * o.tol * S.bb && prev[b] > 0.0 && S.rr_true > 1e-2 * prev[b]) stagnated = true;
-            }
-            if (stagnated) {
-                // switch to FP64 sweeps for one final round
-                cur64 = 1;
-                RCK(prec_setup(w, P, o, 1, &ps, &part));
-                ra.u = ps.u[0];
-                ra.p = ps.p[0];
-                ra.p_other = ps.p[1];
-                ra.keep_p = 0;
-                sa.x = P.x_hi;
-                restart = 1;
-                CK(counted(launch_residual(1, ra, nullptr, w->stream)));
-                CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
-                max_rounds = r + 2;
-                R->fp64_fallback = 1;
-            }
+        CK(cudaMemcpyAsync(h.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+        // FP32 sweeps failed a system when its round ended in a breakdown or
+        // cut its true residual by less than 100x: finish with FP64 sweeps.
+        // An FP64 round that ended in a breakdown gets one restart.
+        bool stagnated = false, broke = false;
+        for (int b = 0; b < bx.nbox; ++b) {
+            const BoxScalars& S = h[b];
+            if (S.nseed == 0 || S.nfree == 0 || !(S.bb > 0.0)) continue;
+            if (!(S.rr_true > o.tol * o.tol * S.bb)) continue;
+            if (S.status == 5) broke = true;
+            if (S.status == 5 || (prev[b] > 0.0 && S.rr_true > 1e-2 * prev[b])) stagnated = true;
+        }
+        if (!cur64 && stagnated) {
+            cur64 = 1;
+            RCK(prec_setup(w, P, o, 1, &ps, &part));
+            ra.u = ps.u[0];
+            ra.p = ps.p[0];
+            ra.p_other = ps.p[1];
+            ra.keep_p = 0;
+            ra.pad = ps.pad;
+            sa.px = sa.py = sa.pz = 0;
+            sa.x = P.x_hi;
+            restart = 1;
+            CK(counted(launch_residual(1, ra, nullptr, w->stream)));
+            CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
+            max_rounds = r + 3;
+            R->fp64_fallback = 1;
+        } else if (cur64 && broke && fp64_restarts < 2) {
+            ++fp64_restarts;
+            restart = 1;
+            max_rounds = std::max(max_rounds, r + 2);
         }
     }
     R->sc.resize(bx.nbox);

@@ -54,6 +54,7 @@ struct SweepArgs {
     double* partials;       // [nbox][tiles][3]
     int* n_active;
     int parity;             // index of the (u, p) buffers this launch reads
+    int px, py, pz;         // padded box dims of the streamed vectors (k_sweep4)
     float c2f;              // -beta * log2(e), FP32 weights
     float wminf;
     double mbeta;           // -beta, FP64 weights
@@ -63,8 +64,10 @@ struct SweepArgs {
 enum GType { G_U16 = 0, G_F32 = 1 };
 enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE_80x8 = 5, TILE_80x16 = 6,
               TILE_32x8 = 7, TILE_32x32 = 8, TILE_64x16 = 9, TILE_W28x28 = 10, TILE_W28x12 = 11, TILE_W28x20 = 12,
-              TILE_W28x28_8W = 13 };
-constexpr int N_TILES = 14;
+              TILE_W28x28_8W = 13, TILE_P32x12 = 14, TILE_P32x12_D4 = 15, TILE_P32x28 = 16, TILE_P40x20 = 17,
+              TILE_P40x8 = 18, TILE_P32x20 = 19 };
+constexpr int N_TILES = 20;
+constexpr int TILE_PADDED_FIRST = TILE_P32x12;  // tiles from here on use the padded layout (k_sweep4)
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
 // combination that is not instantiated.
@@ -74,6 +77,18 @@ void tile_dims(int tile, int* tx, int* ty);
 int sweep_threads(int tile);
 cudaError_t sweep_prepare(int fp64, int gtype, int tile);  // opt-in dynamic smem
 int sweep_occupancy(int fp64, int gtype, int tile);         // resident CTAs per SM (0: not instantiated)
+
+// Padded layout of the vectors streamed by k_sweep4: a box is [pz][py][px]
+// and user voxel (x, y, z) sits at (x + 2, y + 2, z + 2).  px = 0: unpadded.
+struct Pad {
+    int px, py, pz;
+};
+
+__host__ __device__ __forceinline__ int64_t vec_index(const Pad& pd, const Boxes& bx, int box, int x, int y,
+                                                      int z) {
+    if (pd.px == 0) return (((int64_t)box * bx.nz + z) * bx.ny + y) * bx.nx + x;
+    return (((int64_t)box * pd.pz + (z + 2)) * pd.py + (y + 2)) * pd.px + (x + 2);
+}
 
 // Residual / initial guess (solve_kernels.cu).
 struct ResidArgs {
@@ -90,6 +105,7 @@ struct ResidArgs {
     void* p_other;         // p buffer 1 (T): source when a system's latest p is there
     const BoxScalars* sc;  // for keep_p: which buffer holds each system's p
     int keep_p;            // 1: residual replacement keeps the search direction
+    Pad pad;               // layout of u, p and delta
     double* part;          // [nbox][blocks][4]: bb, rr, nseed, nfree
     int blocks_per_box;
     double mbeta, wmin;
@@ -97,7 +113,8 @@ struct ResidArgs {
 cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s);
 // fp64 = 0: also clears the FP32 correction vector `delta`.
 cudaError_t launch_residual(int fp64, const ResidArgs& a, float* delta, cudaStream_t s);
-cudaError_t launch_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x, cudaStream_t s);
+cudaError_t launch_accumulate(const Boxes& bx, const Pad& pad, const uint8_t* code, const float* delta, double* x,
+                              cudaStream_t s);
 cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, BoxScalars* sc, int first,
                               cudaStream_t s);
 cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
@@ -106,8 +123,8 @@ cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, co
                               cudaStream_t s);
 cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s);
 // Pack g and the seed code of every voxel into one word for the FP32 sweep.
-cudaError_t launch_pack_gc(const Boxes& bx, const void* g, int gtype, const uint8_t* code, uint32_t* gc,
-                           cudaStream_t s);
+cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
+                           uint32_t* gc, cudaStream_t s);
 
 // Normalisation / quantisation (hier_kernels.cu).
 cudaError_t launch_quantize(const void* v, int dtype, int64_t n, float lo, float hi, int normalize, int storage,

@@ -19,6 +19,10 @@ cudaError_t sweep3_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s
 cudaError_t sweep3_prepare(int tile);
 int sweep3_occupancy(int tile);
 size_t sweep3_smem(int tile);
+cudaError_t sweep4_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep4_prepare(int tile);
+int sweep4_occupancy(int tile);
+size_t sweep4_smem(int tile);
 cudaError_t sweep_launch_d64_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_launch_d64_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_prepare_d64_u16(int tile);
@@ -48,21 +52,24 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
         return 0;
     }
     if (fp64) slot = gtype == G_U16 ? sweep_occupancy_d64_u16(tile) : sweep_occupancy_d64_f32(tile);
+    else if (tile >= TILE_PADDED_FIRST) slot = sweep4_occupancy(tile);
     else slot = tile >= TILE_W28x28 ? sweep3_occupancy(tile) : sweep2_occupancy(tile);
     return slot;
 }
 
 
 void tile_dims(int tile, int* tx, int* ty) {
-    static const int T[N_TILES][2] = {{0, 0},   {32, 16}, {64, 8},  {40, 8},  {40, 20}, {80, 8}, {80, 16},
-                                      {32, 8},  {32, 32}, {64, 16}, {28, 28}, {28, 12}, {28, 20}, {28, 28}};
+    static const int T[N_TILES][2] = {{0, 0},   {32, 16}, {64, 8},  {40, 8},  {40, 20}, {80, 8},  {80, 16},
+                                      {32, 8},  {32, 32}, {64, 16}, {28, 28}, {28, 12}, {28, 20}, {28, 28},
+                                      {32, 12}, {32, 12}, {32, 28}, {40, 20}, {40, 8},  {32, 20}};
     if (tile < 1 || tile >= N_TILES) tile = 1;
     *tx = T[tile][0];
     *ty = T[tile][1];
 }
 
 int sweep_threads(int tile) {
-    static const int N[N_TILES] = {0, 512, 512, 320, 800, 640, 640, 256, 1024, 1024, 512, 256, 256, 256};
+    static const int N[N_TILES] = {0,   512, 512, 320, 800, 640, 640, 256, 1024, 1024,
+                                   512, 256, 256, 256, 288, 288, 576, 352, 352, 288};
     return (tile >= 1 && tile < N_TILES) ? N[tile] : 0;
 }
 
@@ -73,16 +80,19 @@ size_t sweep_smem_bytes(int fp64, int tile) {
     tile_dims(tile, &tx, &ty);
     const int r2 = (tx + 4) * (ty + 4);
     if (fp64) return (size_t)sweep_planes_bytes<double>(r2);
+    if (tile >= TILE_PADDED_FIRST) return sweep4_smem(tile);
     return tile >= TILE_W28x28 ? sweep3_smem(tile) : sweep2_smem(tile);
 }
 
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     if (fp64) return gtype == G_U16 ? sweep_launch_d64_u16(tile, a, grid, s) : sweep_launch_d64_f32(tile, a, grid, s);
+    if (tile >= TILE_PADDED_FIRST) return sweep4_launch(tile, a, grid, s);
     return tile >= TILE_W28x28 ? sweep3_launch(tile, a, grid, s) : sweep2_launch(tile, a, grid, s);
 }
 
 cudaError_t sweep_prepare(int fp64, int gtype, int tile) {
     if (fp64) return gtype == G_U16 ? sweep_prepare_d64_u16(tile) : sweep_prepare_d64_f32(tile);
+    if (tile >= TILE_PADDED_FIRST) return sweep4_prepare(tile);
     return tile >= TILE_W28x28 ? sweep3_prepare(tile) : sweep2_prepare(tile);
 }
 
@@ -139,6 +149,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
         int ex, ey, ez;
         box_extent(a.bx, box, &ex, &ey, &ez);
         const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+        // (u, p, delta follow a.pad; x_hi, g and the code the caller layout)
         const int64_t base = (int64_t)box * nvox;
         const int64_t i = base + li;
         const double* xh = static_cast<const double*>(a.x);
@@ -173,10 +184,11 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                 uo = d > 0.0 ? (T)(r / d) : (T)0;
             }
         }
-        static_cast<T*>(a.u)[i] = uo;
-        if (!a.keep_p) static_cast<T*>(a.p)[i] = (T)0;
-        else if (a.sc[box].par == 1) static_cast<T*>(a.p)[i] = static_cast<const T*>(a.p_other)[i];
-        if (delta) delta[i] = 0.0f;
+        const int64_t v = vec_index(a.pad, a.bx, box, x, y, z);
+        static_cast<T*>(a.u)[v] = uo;
+        if (!a.keep_p) static_cast<T*>(a.p)[v] = (T)0;
+        else if (a.sc[box].par == 1) static_cast<T*>(a.p)[v] = static_cast<const T*>(a.p_other)[v];
+        if (delta) delta[v] = 0.0f;
     }
     __shared__ double red[4][8];
 #pragma unroll
@@ -311,20 +323,30 @@ cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, co
 }
 
 // x_hi += delta on free voxels (end of a mixed-precision round).
-__global__ void k_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && code[i] == FREE) x[i] += (double)delta[i];
+__global__ void k_accumulate(const Boxes bx, const Pad pad, const uint8_t* code, const float* delta, double* x) {
+    const int box = blockIdx.y;
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nvox) return;
+    const int64_t i = (int64_t)box * nvox + li;
+    if (code[i] != FREE) return;
+    const int xx = (int)(li % bx.nx), yy = (int)((li / bx.nx) % bx.ny), zz = (int)(li / ((int64_t)bx.nx * bx.ny));
+    x[i] += (double)delta[vec_index(pad, bx, box, xx, yy, zz)];
 }
 
-cudaError_t launch_accumulate(int64_t n, const uint8_t* code, const float* delta, double* x, cudaStream_t s) {
-    k_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, code, delta, x);
+cudaError_t launch_accumulate(const Boxes& bx, const Pad& pad, const uint8_t* code, const float* delta, double* x,
+                              cudaStream_t s) {
+    const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
+    dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)bx.nbox);
+    k_accumulate<<<grid, 256, 0, s>>>(bx, pad, code, delta, x);
     return cudaGetLastError();
 }
 
 // gc = (bits of FP32 g with the two low bits cleared) | code', where
 // code' = 1 free, 2 seed, 0 absent (also for voxels beyond the box extent),
 // so that zero-filled halo words read as absent voxels.
-__global__ void k_pack_gc(const Boxes bx, const void* g, int gtype, const uint8_t* code, uint32_t* gc) {
+__global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtype, const uint8_t* code,
+                          uint32_t* gc) {
     const int box = blockIdx.y;
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
     const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -341,14 +363,14 @@ __global__ void k_pack_gc(const Boxes bx, const void* g, int gtype, const uint8_
         const uint32_t cc = c == FREE ? 1u : (c == SEED ? 2u : 0u);
         w = cc ? ((__float_as_uint(gv) & ~3u) | cc) : 0u;
     }
-    gc[i] = w;
+    gc[vec_index(pad, bx, box, x, y, z)] = w;
 }
 
-cudaError_t launch_pack_gc(const Boxes& bx, const void* g, int gtype, const uint8_t* code, uint32_t* gc,
-                           cudaStream_t s) {
+cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
+                           uint32_t* gc, cudaStream_t s) {
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
     dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)bx.nbox);
-    k_pack_gc<<<grid, 256, 0, s>>>(bx, g, gtype, code, gc);
+    k_pack_gc<<<grid, 256, 0, s>>>(bx, pad, g, gtype, code, gc);
     return cudaGetLastError();
 }
 

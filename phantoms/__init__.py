@@ -73,6 +73,35 @@ def normal(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
 
 
+def _hash_torch(seed: int, stream: int, idx):
+    """hash_u64 on a torch int64 tensor (two's-complement wrap-around; logical
+    shifts emulated with masks): the same bits as the numpy path."""
+    import torch
+
+    def srl(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    def s64(v):
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    z = idx ^ s64(_key(seed, stream))
+    z = z + s64(0x9E3779B97F4A7C15)
+    z = (z ^ srl(z, 30)) * s64(0xBF58476D1CE4E5B9)
+    z = (z ^ srl(z, 27)) * s64(0x94D049BB133111EB)
+    return z ^ srl(z, 31)
+
+
+def uniform_torch(seed: int, stream: int, idx):
+    return (((_hash_torch(seed, stream, idx) >> 11) & ((1 << 53) - 1)).double()) * (1.0 / 9007199254740992.0)
+
+
+def normal_torch(seed: int, stream: int, idx):
+    import math as _m
+    u1 = 1.0 - uniform_torch(seed, 2 * stream + 1000, idx)
+    u2 = uniform_torch(seed, 2 * stream + 1001, idx)
+    return (-2.0 * u1.log()).sqrt() * (2.0 * _m.pi * u2).cos()
+
+
 class Stream:
     """Scalar draws from the same counter-based generator (host-side geometry)."""
 
@@ -270,7 +299,7 @@ def _seg_dist2(px, py, pz, a, b):
 
 
 def vessel_tree(n=1024, seed=0, n_segments=200, r_max=12.0, r_min=2.0, shape=None,
-                fg=(3000.0, 400.0), bg=(800.0, 300.0), salt=0.01, salt_value=5000):
+                fg=(3000.0, 400.0), bg=(800.0, 300.0), salt=0.01, salt_value=5000, device=None):
     """Branching vessel tree phantom (uint16) with labels.
 
     Breadth-first bifurcation from a root at a random border point: each segment
@@ -336,10 +365,27 @@ def vessel_tree(n=1024, seed=0, n_segments=200, r_max=12.0, r_min=2.0, shape=Non
                            (px - b[0]) ** 2 + (py - b[1]) ** 2 + (pz - b[2]) ** 2)
         mask[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] |= dist2 <= r * r
 
-    vol = np.empty(shape, dtype=np.uint16)
     plane = nx * ny
+    if device is not None:
+        # same values drawn on the GPU (torch), returned as a uint16 tensor there
+        import torch
+        vol_t = torch.empty(shape, dtype=torch.int32, device=device)
+        mask_t = torch.from_numpy(mask).to(device)
+        zslab = max(1, (1 << 25) // plane)
+        for z0 in range(0, nz, zslab):
+            z1 = min(nz, z0 + zslab)
+            idx = torch.arange(z0 * plane, z1 * plane, dtype=torch.int64, device=device)
+            gn = normal_torch(seed, 3, idx)
+            m = mask_t[z0:z1].reshape(-1)
+            v = torch.where(m, fg[0] + fg[1] * gn, bg[0] + bg[1] * gn)
+            sl = uniform_torch(seed, 4, idx) < salt
+            v = torch.where(sl, torch.full_like(v, float(salt_value)), v)
+            vol_t[z0:z1] = v.round().clamp(0, 65535).to(torch.int32).reshape(z1 - z0, ny, nx)
+        vol = vol_t.to(torch.uint16) if hasattr(torch, "uint16") else vol_t
+    else:
+        vol = np.empty(shape, dtype=np.uint16)
     zslab = max(1, (1 << 22) // plane)
-    for z0 in range(0, nz, zslab):
+    for z0 in (range(0, nz, zslab) if device is None else []):
         z1 = min(nz, z0 + zslab)
         idx = np.arange(z0 * plane, z1 * plane, dtype=np.uint64)
         g = normal(seed, 3, idx)
