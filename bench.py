@@ -4,7 +4,7 @@ One step = one complete rw_solve (normalisation/quantisation, FP32 PCG with
 FP64 reductions, FP64-residual refinement to ||r|| <= 1e-8 ||b||) on inputs
 already resident in HBM.  Metric: voxel-CG-iterations/s = sum over the step of
 free voxels x PCG iterations, divided by the device time (CUDA events, max
-over ranks).  The 256^3 working set streamed per sweep (about 370 MB) is
+over ranks).  The 256^3 working set streamed per sweep (about 470 MB) is
 larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -32,7 +32,7 @@ UNIT = "voxel-iter/s"
 N = int(os.environ.get("RW_BENCH_N", "256"))
 BETA = 130.0
 TOL = 1e-8
-SWEEP_BYTES_PER_VOXEL = 27   # x(delta) r+w 8, u r+w 8, p r+w 8, g 2, code 1  (FP32 vectors, unorm16 g)
+SWEEP_BYTES_PER_VOXEL = 28   # delta r+w 8, u r+w 8, p r+w 8, packed g|code 4  (FP32 vectors)
 WORKLOAD = f"plain random walker, {N}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
 
 
@@ -242,10 +242,10 @@ def run(args):
                        "precision": "FP32 vectors/stencil, FP64 reductions + FP64-residual refinement",
                        "tol": TOL, "iters_per_solve": stats[0]["iters"], "refine_rounds": stats[0]["refine_rounds"],
                        "rel_resid": stats[0]["rel_resid"], "replicas": ws,
-                       "l2": "inputs larger than L2 (about 370 MB streamed per sweep), no flush"},
+                       "l2": "inputs larger than L2 (about 470 MB streamed per sweep), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_sweep (fused PCG sweep)", "peak_source": src,
+                         "kernel": "k_sweep4 (fused PCG sweep)", "peak_source": src,
                          "algorithmic_bytes_per_launch": alg, "launch_ms": t_launch_s * 1e3,
                          "sweeps_per_step": sweeps / args.steps},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}

@@ -68,7 +68,7 @@ double now_ms() {
 enum Slot {
     S_G, S_U0, S_U1, S_P0, S_P1, S_DELTA, S_XHI, S_PART, S_RPART, S_SC, S_NACT, S_VOL, S_CODE, S_VAL, S_X0, S_OUT,
     S_RHS, S_EXT, S_JOBS, S_LAB, S_BFLAGS, S_STATS, S_POOL_G, S_POOL_CODE, S_POOL_X, S_ADJ_PART, S_DBETA, S_DG,
-    S_XF, S_STATUS, S_GC, S_COUNT
+    S_XF, S_STATUS, S_GC, S_LIST, S_COUNT
 };
 
 struct DevWorkspace {
@@ -185,10 +185,13 @@ rw_status check_volume(const rw_volume* v, int64_t* nvox, int64_t* batch) {
 // ---------------------------------------------------------------------------
 // Sweep configuration and the autotuner (tile shape, z-chunk, sweeps per graph).
 struct SweepCfg {
-    int tile = 1, tx = 32, ty = 16, nt = 512, zc = 64, ntx = 1, nty = 1, nzc = 1, grid = 1, ipg = 32;
+    int tile = 1, tx = 32, ty = 16, nt = 512, zc = 64, ntx = 1, nty = 1, nzc = 1, grid = 1, ipg = 32, waves = 0;
 };
 
-std::map<std::string, std::pair<int, int>> g_tuned;  // class -> (tile, iters per graph)
+struct Tuned {
+    int tile, ipg, waves;
+};
+std::map<std::string, Tuned> g_tuned;  // problem class -> autotuned sweep configuration
 
 std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     // one list holds tiles of one layout family only (the autotuner times
@@ -211,7 +214,9 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     return ok;
 }
 
-rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int ipg, SweepCfg* c) {
+// waves = 0: enough z-chunks for two CTAs per resident slot; waves = k >= 1:
+// as many z-chunks as fill k whole waves of the persistent grid (no idle tail).
+rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int ipg, SweepCfg* c, int waves = 0) {
     if (sweep_occupancy(fp64, gtype, tile) <= 0) {
         return fail(RW_ERR_INVALID_ARG, "sweep tile %d not available for this precision/storage", tile);
     }
@@ -224,9 +229,12 @@ rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int 
     const int occ = std::max(1, sweep_occupancy(fp64, gtype, tile));
     const int64_t want = (int64_t)2 * occ * sms;
     const int64_t per_plane = (int64_t)bx.nbox * c->ntx * c->nty;
+    const int64_t slots = (int64_t)occ * sms;
     int nzc = (int)std::max<int64_t>(1, (want + per_plane - 1) / per_plane);
+    if (waves > 0) nzc = (int)std::max<int64_t>(1, (waves * slots) / per_plane);
     int zc = (bx.nz + nzc - 1) / nzc;
-    zc = std::max(zc, std::min(bx.nz, 16));
+    zc = std::max(zc, std::min(bx.nz, 8));
+    c->waves = waves;
     c->zc = zc;
     c->nzc = (bx.nz + zc - 1) / zc;
     const int64_t nwork = per_plane * c->nzc;
@@ -268,37 +276,90 @@ struct SolveResult {
     int fp64_fallback = 0;
 };
 
-rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* const u[2], void* const p[2],
-                           int fp64, int gtype, int* n_active_dev, int64_t* sweeps, int64_t cap, double* ms_dev) {
-    cudaGraph_t graph = nullptr;
+// Configuration of a sweep over `nact` compacted systems: the z-splitting is
+// deepened so that the systems still iterating fill the GPU again.
+void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, int sms, size_t part_elems,
+                 SweepCfg* c) {
+    *c = full;
+    const int occ = std::max(1, sweep_occupancy(fp64, gtype, full.tile));
+    const int64_t slots = (int64_t)occ * sms;
+    const int64_t per_plane = (int64_t)nact * full.ntx * full.nty;
+    int64_t nzc = std::max<int64_t>(full.nzc, (2 * slots + per_plane - 1) / per_plane);
+    nzc = std::min<int64_t>(nzc, std::max(1, (nz + 3) / 4));                       // chunks of >= 4 planes
+    nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, (int64_t)(part_elems / 6) / per_plane));  // partials fit
+    const int zc = (int)((nz + nzc - 1) / nzc);
+    c->zc = zc;
+    c->nzc = (nz + zc - 1) / zc;
+    c->grid = (int)std::max<int64_t>(1, std::min<int64_t>(per_plane * c->nzc, slots));
+    c->ipg = std::min(32, full.ipg * 2);
+}
+
+// Replay graph chunks of cfg.ipg sweeps until no system is active.  Whenever
+// the number of active systems has halved, the active ones are compacted into
+// a list (ascending) and the following sweeps visit only them, with a deeper
+// z-splitting: the slow systems of a batch then no longer run at the width
+// the whole batch was tiled for.
+rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, void* const u[2], void* const p[2],
+                           int fp64, int gtype, int* n_active_dev, int n_act0, int* list_dev, size_t part_elems,
+                           int64_t* sweeps, int64_t cap, double* ms_dev) {
+    SweepCfg cfg = cfg0;
+    sa.list = nullptr;
+    sa.nlist = nullptr;
+    int n_cur = sa.bx.nbox;
     cudaGraphExec_t exec = nullptr;
-    CK(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
-    int par = 0;
-    cudaError_t le = cudaSuccess;
-    for (int j = 0; j < cfg.ipg; ++j) {
-        sa.u_in = u[par];
-        sa.p_in = p[par];
-        sa.u_out = u[par ^ 1];
-        sa.p_out = p[par ^ 1];
-        sa.parity = par;
-        cudaError_t e = launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream);
-        if (e != cudaSuccess && le == cudaSuccess) le = e;
-        par ^= 1;
+    auto capture = [&]() -> rw_status {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
+        int par = 0;
+        cudaError_t le = cudaSuccess;
+        for (int j = 0; j < cfg.ipg; ++j) {
+            sa.u_in = u[par];
+            sa.p_in = p[par];
+            sa.u_out = u[par ^ 1];
+            sa.p_out = p[par ^ 1];
+            sa.parity = par;
+            cudaError_t e = launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream);
+            if (e != cudaSuccess && le == cudaSuccess) le = e;
+            par ^= 1;
+        }
+        cudaError_t ce = cudaStreamEndCapture(w->stream, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            CK(le);
+        }
+        CK(ce);
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        return RW_OK;
+    };
+    auto compact = [&](int n_act) -> rw_status {
+        if (!list_dev || sa.bx.nbox < 2 || n_act <= 0 || 2 * n_act > n_cur) return RW_OK;
+        CK(counted(launch_compact_active(sa.sc, sa.bx.nbox, list_dev, list_dev + sa.bx.nbox, w->stream)));
+        SweepCfg c2;
+        compact_cfg(cfg0, fp64, gtype, sa.bx.nz, n_act, w->sms, part_elems, &c2);
+        cfg = c2;
+        sa.ntx = cfg.ntx;
+        sa.nty = cfg.nty;
+        sa.nzc = cfg.nzc;
+        sa.zc = cfg.zc;
+        sa.list = list_dev;
+        sa.nlist = list_dev + sa.bx.nbox;
+        n_cur = n_act;
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        return capture();
+    };
+    rw_status st = compact(n_act0);
+    if (st == RW_OK && !exec) st = capture();
+    if (st != RW_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        return st;
     }
-    cudaError_t ce = cudaStreamEndCapture(w->stream, &graph);
-    if (le != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        CK(le);
-    }
-    CK(ce);
-    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(ie);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
     int n_act = 1;
-    rw_status st = RW_OK;
     while (n_act > 0 && *sweeps < cap) {
         cudaError_t e = cudaEventRecord(ev0, w->stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(exec, w->stream);
@@ -316,10 +377,14 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, v
         *sweeps += cfg.ipg;
         g_launches += cfg.ipg;
         n_act = *w->pinned;
+        if (n_act > 0 && *sweeps < cap) {
+            st = compact(n_act);
+            if (st != RW_OK) break;
+        }
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    cudaGraphExecDestroy(exec);
+    if (exec) cudaGraphExecDestroy(exec);
     return st;
 }
 
@@ -358,6 +423,7 @@ struct PrecState {
     void* u[2] = {nullptr, nullptr};
     void* p[2] = {nullptr, nullptr};
     SweepCfg cfg;
+    size_t part_elems = 0;  // doubles in the per-CTA partials buffer
     std::vector<int> cands;
     std::string key;
     bool tune = false;
@@ -403,6 +469,7 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     }
     int tile = ps->cands[0];
     int ipg = std::max(2, o.iters_per_graph & ~1);
+    int waves = 0;
     ps->tune = false;
     if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0 &&
         std::find(ps->cands.begin(), ps->cands.end(), o.tile) != ps->cands.end()) {
@@ -410,20 +477,23 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     } else if (o.tile == RW_TILE_AUTO) {
         auto it = g_tuned.find(ps->key);
         if (it != g_tuned.end()) {
-            tile = it->second.first;
-            ipg = it->second.second;
+            tile = it->second.tile;
+            ipg = it->second.ipg;
+            waves = it->second.waves;
         } else {
-            ps->tune = ps->cands.size() > 1;
+            ps->tune = true;
         }
     }
-    RCK(make_cfg(fp64, P.gtype, tile, bx, w->sms, ipg, &ps->cfg));
+    RCK(make_cfg(fp64, P.gtype, tile, bx, w->sms, ipg, &ps->cfg, waves));
     size_t part_elems = (size_t)bx.nbox * ps->cfg.ntx * ps->cfg.nty * ps->cfg.nzc * 6;
-    for (int t : ps->cands) {
-        SweepCfg c2;
-        RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2));
-        part_elems = std::max(part_elems, (size_t)bx.nbox * c2.ntx * c2.nty * c2.nzc * 6);
-    }
+    for (int t : ps->cands)
+        for (int wv = 0; wv <= 4; ++wv) {
+            SweepCfg c2;
+            RCK(make_cfg(fp64, P.gtype, t, bx, w->sms, ipg, &c2, wv));
+            part_elems = std::max(part_elems, (size_t)bx.nbox * c2.ntx * c2.nty * c2.nzc * 6);
+        }
     RCK(ws_get_t(w, S_PART, part_elems * sizeof(double), part));
+    ps->part_elems = part_elems;
     return RW_OK;
 }
 
@@ -433,28 +503,37 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
 // 1 ms of sweeps.
 rw_status autotune(DevWorkspace* w, const SolveProblem& P, PrecState* ps, const SweepArgs& sa, SolveResult* R) {
     float best = 1e30f;
-    int best_tile = ps->cfg.tile;
+    int best_tile = ps->cfg.tile, best_waves = 0;
+    // each distinct (tile, z-chunking) pair runs 4 real sweeps
     for (int t : ps->cands) {
-        SweepCfg c2;
-        RCK(make_cfg(ps->fp64, P.gtype, t, P.bx, w->sms, ps->cfg.ipg, &c2));
-        SweepArgs s2 = sa;
-        s2.ntx = c2.ntx;
-        s2.nty = c2.nty;
-        s2.nzc = c2.nzc;
-        s2.zc = c2.zc;
-        float ms = 0;
-        RCK(time_tile(w, c2, s2, ps->u, ps->p, ps->fp64, P.gtype, 4, &ms));
-        R->sweeps += 4;
-        if (ms < best) {
-            best = ms;
-            best_tile = t;
+        int seen_nzc[5] = {-1, -1, -1, -1, -1};
+        for (int wv = 0; wv <= 4; ++wv) {
+            SweepCfg c2;
+            RCK(make_cfg(ps->fp64, P.gtype, t, P.bx, w->sms, ps->cfg.ipg, &c2, wv));
+            bool dup = false;
+            for (int k = 0; k < wv; ++k) dup = dup || seen_nzc[k] == c2.nzc;
+            seen_nzc[wv] = c2.nzc;
+            if (dup) continue;
+            SweepArgs s2 = sa;
+            s2.ntx = c2.ntx;
+            s2.nty = c2.nty;
+            s2.nzc = c2.nzc;
+            s2.zc = c2.zc;
+            float ms = 0;
+            RCK(time_tile(w, c2, s2, ps->u, ps->p, ps->fp64, P.gtype, 4, &ms));
+            R->sweeps += 4;
+            if (ms < best) {
+                best = ms;
+                best_tile = t;
+                best_waves = wv;
+            }
         }
     }
     const float per = best / 4.0f;
     int k = (int)std::lround(1.0 / std::max(per, 1e-4f));
     k = std::max(8, std::min(64, k)) & ~1;
-    RCK(make_cfg(ps->fp64, P.gtype, best_tile, P.bx, w->sms, k, &ps->cfg));
-    g_tuned[ps->key] = std::make_pair(best_tile, k);
+    RCK(make_cfg(ps->fp64, P.gtype, best_tile, P.bx, w->sms, k, &ps->cfg, best_waves));
+    g_tuned[ps->key] = Tuned{best_tile, k, best_waves};
     ps->tune = false;
     return RW_OK;
 }
@@ -474,6 +553,8 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     double *rpart = nullptr, *part = nullptr;
     RCK(ws_get_t(w, S_SC, bx.nbox * sizeof(BoxScalars), &sc));
     RCK(ws_get_t(w, S_NACT, 64, &nact));
+    int* list = nullptr;
+    RCK(ws_get_t(w, S_LIST, (bx.nbox + 1) * sizeof(int), &list));
     const int bpb = (int)((nvox + 255) / 256);
     RCK(ws_get_t(w, S_RPART, (size_t)bx.nbox * bpb * 4 * sizeof(double), &rpart));
     PrecState ps;
@@ -515,7 +596,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 1, w->stream)));
     CK(counted(launch_zero_homog(cur64, bx, P.code, sc, P.x_hi, w->stream)));
 
-    SweepArgs sa;
+    SweepArgs sa{};
     sa.bx = bx;
     sa.g = P.g;
     sa.code = P.code;
@@ -557,7 +638,8 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
         sa.nzc = ps.cfg.nzc;
         sa.zc = ps.cfg.zc;
         const int64_t cap = R->sweeps + (int64_t)o.max_iter + 4 * ps.cfg.ipg;
-        RCK(run_graph_chunks(w, ps.cfg, sa, ps.u, ps.p, cur64, P.gtype, nact, &R->sweeps, cap, &R->ms_sweeps));
+        RCK(run_graph_chunks(w, ps.cfg, sa, ps.u, ps.p, cur64, P.gtype, nact, *w->pinned, list, ps.part_elems,
+                             &R->sweeps, cap, &R->ms_sweeps));
         // residual replacement: x_hi absorbs the FP32 correction, the FP64
         // residual replaces the recursive one and the search direction is kept
         if (!cur64) CK(counted(launch_accumulate(bx, ps.pad, P.code, delta, P.x_hi, w->stream)));

@@ -51,8 +51,10 @@ struct SweepArgs {
     void* u_out;            // u_k+1 (T)
     void* p_out;            // p_k   (T)
     BoxScalars* sc;
-    double* partials;       // [nbox][tiles][3]
+    double* partials;       // [list position or box][tiles][6]
     int* n_active;
+    const int* list = nullptr;   // optional: the systems to sweep (ascending box indices), else all
+    const int* nlist = nullptr;  // length of `list` (device), read by every launch
     int parity;             // index of the (u, p) buffers this launch reads
     int px, py, pz;         // padded box dims of the streamed vectors (k_sweep4)
     float c2f;              // -beta * log2(e), FP32 weights
@@ -122,6 +124,8 @@ cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, 
 cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, const BoxScalars* sc, void* x,
                               cudaStream_t s);
 cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s);
+// list <- the active systems in ascending order, *nlist <- their number (one CTA).
+cudaError_t launch_compact_active(const BoxScalars* sc, int nbox, int* list, int* nlist, cudaStream_t s);
 // Pack g and the seed code of every voxel into one word for the FP32 sweep.
 cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
                            uint32_t* gc, cudaStream_t s);

@@ -208,8 +208,7 @@ extern "C" rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* 
     NCK(launch_zero_homog(0, bx, seeds->code, sc, xhi, s));
     launches += 6;
 
-    SweepArgs sa;
-    memset(&sa, 0, sizeof(sa));
+    SweepArgs sa{};
     sa.bx = bx;
     sa.ntx = ntx;
     sa.nty = nty;

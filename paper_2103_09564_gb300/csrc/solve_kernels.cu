@@ -322,6 +322,39 @@ cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, co
     return cudaGetLastError();
 }
 
+// Ordered compaction of the active systems: one CTA scans the box records in
+// chunks of its size (ballot within a warp, warp counts through shared memory).
+__global__ void __launch_bounds__(1024) k_compact_active(const BoxScalars* sc, int nbox, int* list, int* nlist) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c = 0; c < nbox; c += blockDim.x) {
+        const int b = c + threadIdx.x;
+        const bool on = b < nbox && sc[b].active;
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int off = base;
+        for (int k = 0; k < warp; ++k) off += wsum[k];
+        if (on) list[off + __popc(m & ((1u << lane) - 1u))] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < nwarp; ++k) tot += wsum[k];
+            base += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nlist = base;
+}
+
+cudaError_t launch_compact_active(const BoxScalars* sc, int nbox, int* list, int* nlist, cudaStream_t s) {
+    k_compact_active<<<1, 1024, 0, s>>>(sc, nbox, list, nlist);
+    return cudaGetLastError();
+}
+
 // x_hi += delta on free voxels (end of a mixed-precision round).
 __global__ void k_accumulate(const Boxes bx, const Pad pad, const uint8_t* code, const float* delta, double* x) {
     const int box = blockIdx.y;

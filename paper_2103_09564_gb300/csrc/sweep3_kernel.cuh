@@ -40,15 +40,16 @@ __global__ void __launch_bounds__(NW * 32, (65536 / (NW * 32 * 64)) > 1 ? (65536
 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, tid = threadIdx.x;
     const int tpb = A.ntx * A.nty * A.nzc;
-    const int64_t nwork = (int64_t)A.bx.nbox * tpb;
+    const int64_t nwork = (int64_t)(A.list ? *A.nlist : A.bx.nbox) * tpb;
     const int nx = A.bx.nx, ny = A.bx.ny, nz = A.bx.nz;
     const int64_t plane = (int64_t)nx * ny;
     const int64_t bstride = plane * nz;
     const float c2 = A.c2f, wmin = A.wminf;
 
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int box = (int)(w / tpb);
-        const int t = (int)(w - (int64_t)box * tpb);
+        const int li = (int)(w / tpb);  // position in the list of active systems
+        const int box = A.list ? A.list[li] : li;
+        const int t = (int)(w - (int64_t)li * tpb);
         BoxScalars* S = A.sc + box;
         if (!S->active) continue;
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
@@ -188,9 +189,9 @@ __global__ void __launch_bounds__(NW * 32, (65536 / (NW * 32 * 64)) > 1 ? (65536
                         if (fr) {
                             const float wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e], wzp = Wzh[e];
                             d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
-                            const float nb = ((wxm * pxl + wxp * pxr) + (wym * P[e - W2] + wyp * P[e + W2])) +
-                                             (wzm * Pl[e] + wzp * Ph[e]);
-                            sv = d * p0 - nb;
+                            // difference form (see k_sweep)
+                            sv = ((wxm * (p0 - pxl) + wxp * (p0 - pxr)) + (wym * (p0 - P[e - W2]) + wyp * (p0 - P[e + W2]))) +
+                                 (wzm * (p0 - Pl[e]) + wzp * (p0 - Ph[e]));
                             if (d > 0.0f) un = U[e] - alpha * __fdividef(sv, d);
                         }
                         Un[e] = un;
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(NW * 32, (65536 / (NW * 32 * 64)) > 1 ? (65536
         double v[6] = {(double)a_gam, (double)a_rr, (double)a_del, (double)a_eps, (double)a_pi, (double)a_tau};
         block_reduce<NT, 6>(v, red);
         if (tid == 0) {
-            double* pp = A.partials + ((int64_t)box * tpb + t) * 6;
+            double* pp = A.partials + ((int64_t)li * tpb + t) * 6;
 #pragma unroll
             for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NW * 32, (65536 / (NW * 32 * 64)) > 1 ? (65536
         if (s_last) {
             __threadfence();
             double tv[6] = {0, 0, 0, 0, 0, 0};
-            const double* pb = A.partials + (int64_t)box * tpb * 6;
+            const double* pb = A.partials + (int64_t)li * tpb * 6;
             for (int k = tid; k < tpb; k += NT)
 #pragma unroll
                 for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);

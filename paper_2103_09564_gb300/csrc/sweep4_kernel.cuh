@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(NT, (65536 / (NT * 64)) > 1 ? (65536 / (NT * 6
 
     const int tid = threadIdx.x;
     const int tpb = A.ntx * A.nty * A.nzc;
-    const int64_t nwork = (int64_t)A.bx.nbox * tpb;
+    const int64_t nwork = (int64_t)(A.list ? *A.nlist : A.bx.nbox) * tpb;
     const int PX = A.px, PY = A.py;
     const int64_t plane = (int64_t)PX * PY;
     const int64_t bstride = plane * A.pz;
@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(NT, (65536 / (NT * 64)) > 1 ? (65536 / (NT * 6
     }
 
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int box = (int)(w / tpb);
-        const int t = (int)(w - (int64_t)box * tpb);
+        const int li = (int)(w / tpb);  // position in the list of active systems
+        const int box = A.list ? A.list[li] : li;
+        const int t = (int)(w - (int64_t)li * tpb);
         BoxScalars* S = A.sc + box;
         if (!S->active) continue;
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
@@ -228,10 +229,11 @@ __global__ void __launch_bounds__(NT, (65536 / (NT * 64)) > 1 ? (65536 / (NT * 6
                         const float wxm = sWx[m4 + e - 1], wxp = sWx[m4 + e], wym = sWy[m4 + e - W2],
                                     wyp = sWy[m4 + e], wzm = sWz[m4 + e], wzp = sWz[h4 + e];
                         const float d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
-                        const float nb = ((wxm * sP[m4 + e - 1] + wxp * sP[m4 + e + 1]) +
-                                          (wym * sP[m4 + e - W2] + wyp * sP[m4 + e + W2])) +
-                                         (wzm * sP[l4 + e] + wzp * sP[h4 + e]);
-                        const float sv = d * p0 - nb;
+                        // difference form (see k_sweep): the weak edges of a
+                        // strongly linked voxel keep their relative precision
+                        const float sv = ((wxm * (p0 - sP[m4 + e - 1]) + wxp * (p0 - sP[m4 + e + 1])) +
+                                          (wym * (p0 - sP[m4 + e - W2]) + wyp * (p0 - sP[m4 + e + W2]))) +
+                                         (wzm * (p0 - sP[l4 + e]) + wzp * (p0 - sP[h4 + e]));
                         const bool isfree = (rG[s + e] & 3u) == 1u && d > 0.0f;
                         const float fr = isfree ? 1.0f : 0.0f;
                         const float inv = isfree ? __fdividef(1.0f, d) : 0.0f;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(NT, (65536 / (NT * 64)) > 1 ? (65536 / (NT * 6
         double v[6] = {(double)a_gam, (double)a_rr, (double)a_del, (double)a_eps, (double)a_pi, (double)a_tau};
         block_reduce<NT, 6>(v, red);
         if (tid == 0) {
-            double* pp = A.partials + ((int64_t)box * tpb + t) * 6;
+            double* pp = A.partials + ((int64_t)li * tpb + t) * 6;
 #pragma unroll
             for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(NT, (65536 / (NT * 64)) > 1 ? (65536 / (NT * 6
         if (s_last) {
             __threadfence();
             double tv[6] = {0, 0, 0, 0, 0, 0};
-            const double* pb = A.partials + (int64_t)box * tpb * 6;
+            const double* pb = A.partials + (int64_t)li * tpb * 6;
             for (int k = tid; k < tpb; k += NT)
 #pragma unroll
                 for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);

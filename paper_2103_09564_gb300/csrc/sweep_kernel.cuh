@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
 
     const int tid = threadIdx.x;
     const int tpb = A.ntx * A.nty * A.nzc;
-    const int64_t nwork = (int64_t)A.bx.nbox * tpb;
+    const int64_t nwork = (int64_t)(A.list ? *A.nlist : A.bx.nbox) * tpb;
     const int nx = A.bx.nx, ny = A.bx.ny, nz = A.bx.nz;
     const int64_t bstride = (int64_t)nx * ny * nz;
     const G* __restrict__ gin = static_cast<const G*>(A.g);
@@ -177,8 +177,9 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
     T* __restrict__ Pout = static_cast<T*>(A.p_out);
 
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int box = (int)(w / tpb);
-        const int t = (int)(w - (int64_t)box * tpb);
+        const int li = (int)(w / tpb);  // position in the list of active systems
+        const int box = A.list ? A.list[li] : li;
+        const int t = (int)(w - (int64_t)li * tpb);
         BoxScalars* S = A.sc + box;
         if (!S->active) continue;  // same value for every thread of the CTA
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
@@ -256,9 +257,12 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
                             const T wxm = Wx[e - 1], wxp = Wx[e], wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e],
                                     wzp = Wzh[e];
                             d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
-                            const T nb = ((wxm * P[e - 1] + wxp * P[e + 1]) + (wym * P[e - W2] + wyp * P[e + W2])) +
-                                         (wzm * Pl[e] + wzp * Ph[e]);
-                            sv = d * p0 - nb;
+                            // difference form: every edge keeps its own
+                            // relative precision (d * p0 - sum w p_j would
+                            // cancel the weak edges of a strongly linked voxel)
+                            sv = ((wxm * (p0 - P[e - 1]) + wxp * (p0 - P[e + 1])) +
+                                  (wym * (p0 - P[e - W2]) + wyp * (p0 - P[e + W2]))) +
+                                 (wzm * (p0 - Pl[e]) + wzp * (p0 - Ph[e]));
                             if (d > (T)0) un = sUk[m2 * R2 + e] - alpha * sv / d;
                         }
                         sUn[m3 * R2 + e] = un;
@@ -300,10 +304,10 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
                         if (u0 != (T)0 && ox + jx - 2 < ex && oy + jy - 2 < ey) {
                             const T wxm = Wx[e - 1], wxp = Wx[e], wym = Wy[e - W2], wyp = Wy[e], wzm = Wzl[e],
                                     wzp = Wzh[e];
-                            const T d = ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
-                            const T nb = ((wxm * U[e - 1] + wxp * U[e + 1]) + (wym * U[e - W2] + wyp * U[e + W2])) +
-                                         (wzm * Ul[e] + wzp * Uh[e]);
-                            a_del += (acc)u0 * (acc)(d * u0 - nb);
+                            const T au = ((wxm * (u0 - U[e - 1]) + wxp * (u0 - U[e + 1])) +
+                                          (wym * (u0 - U[e - W2]) + wyp * (u0 - U[e + W2]))) +
+                                         (wzm * (u0 - Ul[e]) + wzp * (u0 - Uh[e]));
+                            a_del += (acc)u0 * (acc)au;
                         }
                     }
                 }
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
         double v[6] = {(double)a_gam, (double)a_rr, (double)a_del, (double)a_eps, (double)a_pi, (double)a_tau};
         block_reduce<NT, 6>(v, red);
         if (tid == 0) {
-            double* pp = A.partials + ((int64_t)box * tpb + t) * 6;
+            double* pp = A.partials + ((int64_t)li * tpb + t) * 6;
 #pragma unroll
             for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
         if (s_last) {
             __threadfence();
             double tv[6] = {0, 0, 0, 0, 0, 0};
-            const double* pb = A.partials + (int64_t)box * tpb * 6;
+            const double* pb = A.partials + (int64_t)li * tpb * 6;
             for (int k = tid; k < tpb; k += NT)
 #pragma unroll
                 for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);

@@ -203,6 +203,32 @@ def plain_ball(n: int = 64, seed: int = 0):
     return ball_case(n=n, seed=seed, radius=20.0 * n / 64.0)
 
 
+def pocket_case(n: int = 24, seed: int = 0, n_pairs: int = 6, bridge: float = 0.6075):
+    """Weakly attached salt pairs: a numerically hard but determined system.
+
+    Background N(0.3, 0.02), clamped; `n_pairs` pairs of adjacent voxels at 1.0
+    (joined by a weight-1 edge at beta = 130), each with one neighbour at
+    `bridge` (edge weight exp(-130 (1 - bridge)^2) ~ 2e-9) and all other exits
+    at ~1e-28.  The common mode of a pair has a Jacobi-scaled eigenvalue
+    ~1e-9: below FP32 resolution, well inside FP64's.  Seeds: the x = 0 face
+    (value 0) and the x = n - 1 face (value 1).  Returns the plain-solve dict
+    plus ``pairs`` (the (z, y, x) of each pair's first voxel)."""
+    shape = (n, n, n)
+    vol = np.clip(0.3 + _voxel_noise(seed, 1, shape, 0.02), 0.0, 1.0)
+    st = Stream(seed, 11)
+    pairs = []
+    for _ in range(n_pairs):
+        z, y, x = (int(st.uniform(3, n - 4)) for _ in range(3))
+        vol[z, y, x] = vol[z, y + 1, x] = 1.0
+        vol[z, y, x + 1] = bridge
+        pairs.append((z, y, x))
+    code = np.zeros(shape, dtype=np.uint8)
+    value = np.zeros(shape, dtype=np.float32)
+    code[:, :, 0] = code[:, :, -1] = 1
+    value[:, :, -1] = 1.0
+    return {"volume": vol.astype(np.float32), "code": code, "value": value, "pairs": pairs, "beta": 130.0}
+
+
 def _polyline(st: Stream, inside, shape, length=40, max_tries=4000):
     nz, ny, nx = shape
     for _ in range(max_tries):

@@ -5,6 +5,7 @@ import pytest
 
 import oracle as O
 import phantoms as P
+from conftest import determined_mask
 from oracle import hrw
 
 pytestmark = pytest.mark.gpu
@@ -62,7 +63,8 @@ def _compare(rw, tree, otree, opts, s, incremental=False):
                     assert abs(ni.maxdiff - opts.t_inc) < NEAR, f"level {k}: similar differs at {b}"
                     excluded.append((k, b))
         field = tree.read_level(k).astype(np.float64)
-        mask = np.ones(field.shape, bool)
+        # trapped pockets (salt clusters behind w_min edges) are undetermined
+        mask = determined_mask(otree.levels[k], opts.beta)
         for (kk, e) in excluded:
             sh = k - kk
             lo = [v * s * (1 << sh) for v in e]
@@ -173,4 +175,8 @@ def test_per_brick_sequential_equals_batched(rw):
     a.run(ph["labels_xyz"], ph["labels_value"])
     b = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11, batch_bricks=0, precision="fp64"))
     b.run(ph["labels_xyz"], ph["labels_value"])
-    assert np.max(np.abs(a.read_level(pyr.levels - 1) - b.read_level(pyr.levels - 1))) <= TOL
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    det = determined_mask(O.leaf_level(q), 130.0)
+    assert det.mean() > 0.99
+    diff = np.abs(a.read_level(pyr.levels - 1) - b.read_level(pyr.levels - 1))
+    assert np.max(diff[det]) <= TOL
