@@ -29,11 +29,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "voxel-CG-iterations/s and HBM GB/s (% of peak) at <=1e-4 prob error vs FP64"
 UNIT = "voxel-iter/s"
-N = int(os.environ.get("RW_BENCH_N", "256"))
 BETA = 130.0
 TOL = 1e-8
-SWEEP_BYTES_PER_VOXEL = 28   # delta r+w 8, u r+w 8, p r+w 8, packed g|code 4  (FP32 vectors)
-WORKLOAD = f"plain random walker, {N}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
+# algorithmic bytes per voxel-iteration (the method's minimum in mixed
+# precision): x, r, p FP32 read + written (24 B), unorm16 g (2 B), seed code
+# (1 B).  The sweep kernel itself moves 28 B (g and code packed in one word).
+SWEEP_BYTES_PER_VOXEL = 27
+KERNEL_BYTES_PER_VOXEL = 28
+def _workload(n):
+    return f"plain random walker, {n}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
 
 
 def _peaks():
@@ -119,7 +123,7 @@ def _cpu_baseline(c, seconds=15.0):
     _, it, _, _ = O.rw_solve(g, c["code"], xin, BETA, tol=1e-13, max_iter=m)
     dt = time.perf_counter() - t0
     return {"value": nfree * it / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle Jacobi-PCG, first {it} iterations of the 256^3 system ({nfree} free voxels), "
+            "sample": f"FP64 oracle Jacobi-PCG, first {it} iterations of the {c['volume'].shape[0]}^3 system ({nfree} free voxels), "
                       f"{dt:.1f} s incl. weight set-up"}
 
 
@@ -129,6 +133,7 @@ def run_reference(args):
         return 0
     import phantoms as P
     import oracle as O
+    N = args.n or 256
     c = P.plain_ellipsoids(n=N, seed=0)
     q = O.quantize(c["volume"])
     g = O.dequantize(q)
@@ -146,7 +151,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "voxels": N ** 3, "free_voxels": nfree,
+            "config": {"workload": _workload(N), "voxels": N ** 3, "free_voxels": nfree,
                        "step": f"{iters_per_step} FP64 PCG iterations of the oracle (plus its weight set-up)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"{iters_per_step} iterations per step x {args.steps} steps"},
@@ -167,6 +172,7 @@ def run(args):
         pg = dist
     import paper_2103_09564_gb300 as rw
     import phantoms as P
+    N = args.n or 256
     c = P.plain_ellipsoids(n=N, seed=0)
     vol = torch.from_numpy(c["volume"]).to(dev)
     code = torch.from_numpy(c["code"]).to(dev)
@@ -233,12 +239,12 @@ def run(args):
         return 0
     peak, src = _peaks()
     t_launch_s = (ms_sweeps / max(sweeps, 1)) / 1e3
-    alg = SWEEP_BYTES_PER_VOXEL * N ** 3
+    alg = SWEEP_BYTES_PER_VOXEL * int(stats[0]["free_voxels"])
     achieved = alg / t_launch_s / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "voxels": N ** 3, "free_voxels": int(stats[0]["free_voxels"]),
+            "config": {"workload": _workload(N), "voxels": N ** 3, "free_voxels": int(stats[0]["free_voxels"]),
                        "precision": "FP32 vectors/stencil, FP64 reductions + FP64-residual refinement",
                        "tol": TOL, "iters_per_solve": stats[0]["iters"], "refine_rounds": stats[0]["refine_rounds"],
                        "rel_resid": stats[0]["rel_resid"], "replicas": ws,
@@ -246,7 +252,8 @@ def run(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "k_sweep4 (fused PCG sweep)", "peak_source": src,
-                         "algorithmic_bytes_per_launch": alg, "launch_ms": t_launch_s * 1e3,
+                         "algorithmic_bytes_per_launch": alg, "basis": "27 B per free voxel per sweep",
+                         "kernel_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL, "launch_ms": t_launch_s * 1e3,
                          "sweeps_per_step": sweeps / args.steps},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
     if ws == 1 and not args.no_cpu_baseline:
@@ -270,7 +277,7 @@ def run_hier(args):
     import torch
     import paper_2103_09564_gb300 as rw
     import phantoms as P
-    n = int(os.environ.get("RW_BENCH_N", "1024"))
+    n = args.n or 1024
     s = args.brick
     dev = torch.device("cuda", 0)
     ph = P.vessel_tree(n=n, seed=0, device=dev)
@@ -302,7 +309,7 @@ def run_hier(args):
     # batched mixed vs per-brick FP64 on the leaf level of a 256^3 phantom
     cmp = _compare_batched_vs_fp64(rw, P, s, args.tol)
     peak, src = _peaks()
-    eff = 28.0 * vi / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+    eff = SWEEP_BYTES_PER_VOXEL * vi / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
     line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -313,7 +320,7 @@ def run_hier(args):
             "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s",
                          "frac": (eff / peak) if eff else None, "traffic": None,
                          "kernel": "fused PCG sweep over the brick batches",
-                         "basis": "28 B per free-voxel iteration / device time of the sweeps", "peak_source": src},
+                         "basis": "27 B per free-voxel iteration / device time of the sweeps", "peak_source": src},
             "batched_vs_per_brick_fp64": cmp, "gpu_launches": int(sum(st["launches"] for st in stats)),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -348,7 +355,7 @@ def run_adjoint(args):
     import torch
     import paper_2103_09564_gb300 as rw
     import phantoms as P
-    n = int(os.environ.get("RW_BENCH_N", "96"))
+    n = args.n or 96
     b = P.adjoint_batch(n=n, batch=32)
     dev = torch.device("cuda", 0)
     g = torch.from_numpy(b["volume"]).to(dev)
@@ -406,6 +413,8 @@ def main():
                          "adjoint: 32 x 96^3 differentiable batch")
     ap.add_argument("--brick", type=int, default=32)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--n", type=int, default=0,
+                    help="volume edge (default: 256 plain, 1024 hier, 96 adjoint; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

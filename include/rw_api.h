@@ -122,7 +122,10 @@ enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, 
        RW_TILE_W28x28 = 10, RW_TILE_W28x12 = 11, RW_TILE_W28x20 = 12, RW_TILE_W28x28_8W = 13,
        /* padded-layout tiles (16-byte asynchronous row copies; FP32 only, the default family) */
        RW_TILE_P32x12 = 14, RW_TILE_P32x12_DEEP = 15, RW_TILE_P32x28 = 16, RW_TILE_P40x20 = 17,
-       RW_TILE_P40x8 = 18, RW_TILE_P32x20 = 19 };
+       RW_TILE_P40x8 = 18, RW_TILE_P32x20 = 19,
+       /* register-blocked strips of 4 voxels (padded layout, x margin 4) */
+       RW_TILE_S64x11 = 20, RW_TILE_S32x22 = 21, RW_TILE_S32x20 = 22, RW_TILE_S64x8 = 23,
+       RW_TILE_S40x20 = 24, RW_TILE_S40x8 = 25 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */

@@ -195,8 +195,9 @@ std::map<std::string, Tuned> g_tuned;  // problem class -> autotuned sweep confi
 
 std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     // one list holds tiles of one layout family only (the autotuner times
-    // them on the same live vectors): padded k_sweep4 tiles, or the unpadded
-    // k_sweep2 tile for boxes narrower than one padded tile
+    // them on the same live vectors): the strip kernel's tiles (padded
+    // layout, x margin 4), or the unpadded k_sweep2 tile for boxes narrower
+    // than one padded tile
     std::vector<int> c;
     (void)gtype;
     if (fp64) {
@@ -204,9 +205,9 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     } else if (nx <= 24) {
         c = {7};
     } else if (nx <= 48 || (nx % 40 == 0 && nx <= 160)) {
-        c = {17, 18};
+        c = {TILE_S40x20, TILE_S40x8};
     } else {
-        c = {14, 15, 19, 16};
+        c = {TILE_S64x11, TILE_S32x22, TILE_S32x20, TILE_S64x8};
     }
     std::vector<int> ok;
     for (int t : c)
@@ -418,7 +419,7 @@ rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* co
 // (autotuned once per problem class), partial-sum storage.
 struct PrecState {
     int fp64 = 0;
-    Pad pad = {0, 0, 0};   // layout of u, p, delta, g|code for this precision
+    Pad pad = {0, 0, 0, 0};   // layout of u, p, delta, g|code for this precision
     int64_t nvec = 0;      // elements of each streamed vector
     void* u[2] = {nullptr, nullptr};
     void* p[2] = {nullptr, nullptr};
@@ -440,10 +441,12 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     if (ps->cands.empty()) return fail(RW_ERR_INVALID_ARG, "no sweep kernel for this precision/storage");
     if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0)
         ps->cands = {o.tile};  // an explicit tile: its own layout, no tuning
-    ps->pad = {0, 0, 0};
+    ps->pad = {0, 0, 0, 0};
     ps->nvec = ntot;
     if (!fp64 && ps->cands[0] >= TILE_PADDED_FIRST) {
-        // padded box: covers whole tiles of every candidate, 2-voxel margins
+        // padded box: covers whole tiles of every candidate; margins of 2
+        // voxels (x: 4 for the strip kernel, whose tiles start 16-byte aligned)
+        const int mx = ps->cands[0] >= TILE_STRIP_FIRST ? 4 : 2;
         int px = 0, py = 0;
         for (int t : ps->cands) {
             int tx, ty;
@@ -451,7 +454,8 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
             px = std::max(px, tx * ((bx.nx + tx - 1) / tx));
             py = std::max(py, ty * ((bx.ny + ty - 1) / ty));
         }
-        ps->pad.px = ((px + 4) + 3) & ~3;
+        ps->pad.mx = mx;
+        ps->pad.px = ((px + 2 * mx) + 3) & ~3;
         ps->pad.py = py + 4;
         ps->pad.pz = bx.nz + 4;
         ps->nvec = (int64_t)ps->pad.px * ps->pad.py * ps->pad.pz * bx.nbox;

@@ -67,9 +67,11 @@ enum GType { G_U16 = 0, G_F32 = 1 };
 enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE_80x8 = 5, TILE_80x16 = 6,
               TILE_32x8 = 7, TILE_32x32 = 8, TILE_64x16 = 9, TILE_W28x28 = 10, TILE_W28x12 = 11, TILE_W28x20 = 12,
               TILE_W28x28_8W = 13, TILE_P32x12 = 14, TILE_P32x12_D4 = 15, TILE_P32x28 = 16, TILE_P40x20 = 17,
-              TILE_P40x8 = 18, TILE_P32x20 = 19 };
-constexpr int N_TILES = 20;
+              TILE_P40x8 = 18, TILE_P32x20 = 19, TILE_S64x11 = 20, TILE_S32x22 = 21, TILE_S32x20 = 22,
+              TILE_S64x8 = 23, TILE_S40x20 = 24, TILE_S40x8 = 25 };
+constexpr int N_TILES = 26;
 constexpr int TILE_PADDED_FIRST = TILE_P32x12;  // tiles from here on use the padded layout (k_sweep4)
+constexpr int TILE_STRIP_FIRST = TILE_S64x11;   // tiles from here on: k_sweep5, padded with x margin 4
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
 // combination that is not instantiated.
@@ -84,12 +86,13 @@ int sweep_occupancy(int fp64, int gtype, int tile);         // resident CTAs per
 // and user voxel (x, y, z) sits at (x + 2, y + 2, z + 2).  px = 0: unpadded.
 struct Pad {
     int px, py, pz;
+    int mx;  // x margin (2, or 4 for the strip kernel); y and z margins are 2
 };
 
 __host__ __device__ __forceinline__ int64_t vec_index(const Pad& pd, const Boxes& bx, int box, int x, int y,
                                                       int z) {
     if (pd.px == 0) return (((int64_t)box * bx.nz + z) * bx.ny + y) * bx.nx + x;
-    return (((int64_t)box * pd.pz + (z + 2)) * pd.py + (y + 2)) * pd.px + (x + 2);
+    return (((int64_t)box * pd.pz + (z + 2)) * pd.py + (y + 2)) * pd.px + (x + pd.mx);
 }
 
 // Residual / initial guess (solve_kernels.cu).

@@ -23,6 +23,10 @@ cudaError_t sweep4_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s
 cudaError_t sweep4_prepare(int tile);
 int sweep4_occupancy(int tile);
 size_t sweep4_smem(int tile);
+cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t sweep5_prepare(int tile);
+int sweep5_occupancy(int tile);
+size_t sweep5_smem(int tile);
 cudaError_t sweep_launch_d64_u16(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_launch_d64_f32(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep_prepare_d64_u16(int tile);
@@ -52,6 +56,7 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
         return 0;
     }
     if (fp64) slot = gtype == G_U16 ? sweep_occupancy_d64_u16(tile) : sweep_occupancy_d64_f32(tile);
+    else if (tile >= TILE_STRIP_FIRST) slot = sweep5_occupancy(tile);
     else if (tile >= TILE_PADDED_FIRST) slot = sweep4_occupancy(tile);
     else slot = tile >= TILE_W28x28 ? sweep3_occupancy(tile) : sweep2_occupancy(tile);
     return slot;
@@ -61,7 +66,8 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
 void tile_dims(int tile, int* tx, int* ty) {
     static const int T[N_TILES][2] = {{0, 0},   {32, 16}, {64, 8},  {40, 8},  {40, 20}, {80, 8},  {80, 16},
                                       {32, 8},  {32, 32}, {64, 16}, {28, 28}, {28, 12}, {28, 20}, {28, 28},
-                                      {32, 12}, {32, 12}, {32, 28}, {40, 20}, {40, 8},  {32, 20}};
+                                      {32, 12}, {32, 12}, {32, 28}, {40, 20}, {40, 8},  {32, 20},
+                                      {64, 11}, {32, 22}, {32, 20}, {64, 8},  {40, 20}, {40, 8}};
     if (tile < 1 || tile >= N_TILES) tile = 1;
     *tx = T[tile][0];
     *ty = T[tile][1];
@@ -69,7 +75,8 @@ void tile_dims(int tile, int* tx, int* ty) {
 
 int sweep_threads(int tile) {
     static const int N[N_TILES] = {0,   512, 512, 320, 800, 640, 640, 256, 1024, 1024,
-                                   512, 256, 256, 256, 288, 288, 576, 352, 352, 288};
+                                   512, 256, 256, 256, 288, 288, 576, 352, 352, 288,
+                                   256, 256, 256, 224, 288, 160};
     return (tile >= 1 && tile < N_TILES) ? N[tile] : 0;
 }
 
@@ -80,18 +87,21 @@ size_t sweep_smem_bytes(int fp64, int tile) {
     tile_dims(tile, &tx, &ty);
     const int r2 = (tx + 4) * (ty + 4);
     if (fp64) return (size_t)sweep_planes_bytes<double>(r2);
+    if (tile >= TILE_STRIP_FIRST) return sweep5_smem(tile);
     if (tile >= TILE_PADDED_FIRST) return sweep4_smem(tile);
     return tile >= TILE_W28x28 ? sweep3_smem(tile) : sweep2_smem(tile);
 }
 
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     if (fp64) return gtype == G_U16 ? sweep_launch_d64_u16(tile, a, grid, s) : sweep_launch_d64_f32(tile, a, grid, s);
+    if (tile >= TILE_STRIP_FIRST) return sweep5_launch(tile, a, grid, s);
     if (tile >= TILE_PADDED_FIRST) return sweep4_launch(tile, a, grid, s);
     return tile >= TILE_W28x28 ? sweep3_launch(tile, a, grid, s) : sweep2_launch(tile, a, grid, s);
 }
 
 cudaError_t sweep_prepare(int fp64, int gtype, int tile) {
     if (fp64) return gtype == G_U16 ? sweep_prepare_d64_u16(tile) : sweep_prepare_d64_f32(tile);
+    if (tile >= TILE_STRIP_FIRST) return sweep5_prepare(tile);
     if (tile >= TILE_PADDED_FIRST) return sweep4_prepare(tile);
     return tile >= TILE_W28x28 ? sweep3_prepare(tile) : sweep2_prepare(tile);
 }

@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(NW * 32, (65536 / (NW * 32 * 64)) > 1 ? (65536
             }
             cp_async_wait<0>();
         }
-        double v[6] = {(double)a_gam, (double)a_rr, (double)a_del, (double)a_eps, (double)a_pi, (double)a_tau};
-        block_reduce<NT, 6>(v, red);
+        const float fv[6] = {a_gam, a_rr, a_del, a_eps, a_pi, a_tau};
+        double v[6];
+        block_reduce_f32<NT, 6>(fv, v, red);
         if (tid == 0) {
             double* pp = A.partials + ((int64_t)li * tpb + t) * 6;
 #pragma unroll

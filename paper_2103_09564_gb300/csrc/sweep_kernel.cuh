@@ -96,6 +96,35 @@ __device__ __forceinline__ void block_reduce(double* v, double* red) {
     __syncthreads();
 }
 
+// Same for FP32 per-thread partials: the 32 lanes of a warp are summed in
+// FP32 (a few roundings on top of each thread's FP32 sum), the warp partials
+// in FP64 and in a fixed order.  Result in v of warp 0.
+template <int NT, int NV>
+__device__ __forceinline__ void block_reduce_f32(const float* f, double* v, double* red) {
+    constexpr int NW = NT / 32;
+    float t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = f[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k * NW + wid] = (double)t[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = lane < NW ? red[k * NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();
+}
+
 // Scalar recurrences of the system after its sweep (run by one thread of the
 // last CTA).  v = {gamma, ||r||^2, delta, eps, pi, tau} of the sweep that
 // produced u = u_k+1 from the direction p = p_k:
