@@ -235,6 +235,7 @@ rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int 
     if (waves > 0) nzc = (int)std::max<int64_t>(1, (waves * slots) / per_plane);
     int zc = (bx.nz + nzc - 1) / nzc;
     zc = std::max(zc, std::min(bx.nz, 8));
+    zc = (zc + 1) & ~1;  // chunks start at even planes (the strip kernel's unrolled z loop)
     c->waves = waves;
     c->zc = zc;
     c->nzc = (bx.nz + zc - 1) / zc;
@@ -288,7 +289,7 @@ void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, in
     int64_t nzc = std::max<int64_t>(full.nzc, (2 * slots + per_plane - 1) / per_plane);
     nzc = std::min<int64_t>(nzc, std::max(1, (nz + 3) / 4));                       // chunks of >= 4 planes
     nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, (int64_t)(part_elems / 6) / per_plane));  // partials fit
-    const int zc = (int)((nz + nzc - 1) / nzc);
+    const int zc = ((int)((nz + nzc - 1) / nzc) + 1) & ~1;  // even, see make_cfg
     c->zc = zc;
     c->nzc = (nz + zc - 1) / zc;
     c->grid = (int)std::max<int64_t>(1, std::min<int64_t>(per_plane * c->nzc, slots));
@@ -591,8 +592,11 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     uint32_t* gc = nullptr;
     if (!cur64) {
         RCK(ws_get_t(w, S_GC, ps.nvec * 4, &gc));
-        if (ps.pad.px) CK(cudaMemsetAsync(gc, 0, ps.nvec * 4, w->stream));
-        CK(counted(launch_pack_gc(bx, ps.pad, P.g, P.gtype, P.code, gc, w->stream)));
+        // the strip kernel's format marks absent voxels (margins included) NaN
+        const int fmt = ps.pad.mx == 4 ? 1 : 0;
+        if (fmt) CK(counted(launch_fill_u32(gc, ps.nvec, GC_ABSENT, w->stream)));
+        else if (ps.pad.px) CK(cudaMemsetAsync(gc, 0, ps.nvec * 4, w->stream));
+        CK(counted(launch_pack_gc(bx, ps.pad, P.g, P.gtype, P.code, gc, w->stream, fmt)));
     }
     CK(cudaMemsetAsync(sc, 0, bx.nbox * sizeof(BoxScalars), w->stream));
     if (P.init_x) CK(counted(launch_init_x(cur64, ra, w->stream)));

@@ -129,9 +129,13 @@ cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, co
 cudaError_t launch_copy_out(int fp64, const Boxes& bx, const void* x, float* out, cudaStream_t s);
 // list <- the active systems in ascending order, *nlist <- their number (one CTA).
 cudaError_t launch_compact_active(const BoxScalars* sc, int nbox, int* list, int* nlist, cudaStream_t s);
-// Pack g and the seed code of every voxel into one word for the FP32 sweep.
+// Pack g and the seed code of every voxel into one word for the FP32 sweep:
+// fmt 0 (k_sweep2/3/4): code in the two lowest mantissa bits; fmt 1
+// (k_sweep5): +g free, -g seed, GC_ABSENT (a NaN) absent.
+constexpr uint32_t GC_ABSENT = 0xffc00000u;
 cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
-                           uint32_t* gc, cudaStream_t s);
+                           uint32_t* gc, cudaStream_t s, int fmt = 0);
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s);
 
 // Normalisation / quantisation (hier_kernels.cu).
 cudaError_t launch_quantize(const void* v, int dtype, int64_t n, float lo, float hi, int normalize, int storage,

@@ -388,8 +388,10 @@ cudaError_t launch_accumulate(const Boxes& bx, const Pad& pad, const uint8_t* co
 // gc = (bits of FP32 g with the two low bits cleared) | code', where
 // code' = 1 free, 2 seed, 0 absent (also for voxels beyond the box extent),
 // so that zero-filled halo words read as absent voxels.
+// fmt 0: FP32 g with the code in its two lowest mantissa bits (0 absent,
+// 1 free, 2 seed); fmt 1: +g free, -g seed, NaN absent (g >= 0).
 __global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtype, const uint8_t* code,
-                          uint32_t* gc) {
+                          uint32_t* gc, int fmt) {
     const int box = blockIdx.y;
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
     const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -398,22 +400,39 @@ __global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtyp
     box_extent(bx, box, &ex, &ey, &ez);
     const int x = (int)(li % bx.nx), y = (int)((li / bx.nx) % bx.ny), z = (int)(li / ((int64_t)bx.nx * bx.ny));
     const int64_t i = (int64_t)box * nvox + li;
-    uint32_t w = 0u;
+    uint32_t w = fmt ? GC_ABSENT : 0u;
     if (x < ex && y < ey && z < ez) {
         const uint8_t c = code[i];
         const float gv = gtype == G_U16 ? (float)static_cast<const uint16_t*>(g)[i] * (1.0f / 65535.0f)
                                         : static_cast<const float*>(g)[i];
-        const uint32_t cc = c == FREE ? 1u : (c == SEED ? 2u : 0u);
-        w = cc ? ((__float_as_uint(gv) & ~3u) | cc) : 0u;
+        if (fmt) {
+            const uint32_t gb = __float_as_uint(fabsf(gv));
+            w = c == FREE ? gb : (c == SEED ? (gb | 0x80000000u) : GC_ABSENT);
+        } else {
+            const uint32_t cc = c == FREE ? 1u : (c == SEED ? 2u : 0u);
+            w = cc ? ((__float_as_uint(gv) & ~3u) | cc) : 0u;
+        }
     }
     gc[vec_index(pad, bx, box, x, y, z)] = w;
 }
 
 cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
-                           uint32_t* gc, cudaStream_t s) {
+                           uint32_t* gc, cudaStream_t s, int fmt) {
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
     dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)bx.nbox);
-    k_pack_gc<<<grid, 256, 0, s>>>(bx, pad, g, gtype, code, gc);
+    k_pack_gc<<<grid, 256, 0, s>>>(bx, pad, g, gtype, code, gc, fmt);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill_u32(uint32_t* p, int64_t n, uint32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 65536);
+    k_fill_u32<<<(unsigned)blocks, 256, 0, s>>>(p, n, v);
     return cudaGetLastError();
 }
 

@@ -6,26 +6,34 @@
 //
 // * A thread owns a strip of four consecutive voxels of one row of the tile
 //   (one 16-byte word of every streamed vector) and marches it through z.
-//   The strip's own values at z-1, z, z+1 (p_k, the g|code words, the z-edge
+//   The strip's own values at z-1, z, z+1 (p_k, the g words, the z-edge
 //   weights) stay in registers; only x/y neighbours are exchanged, through
 //   double-buffered shared planes read with 128-bit loads (the strip ends
 //   through small per-strip arrays).
 // * Every edge weight is evaluated once per plane, by the voxel that owns the
 //   edge as its forward (+x, +y, +z) edge; the backward weights of a voxel
 //   are its neighbours' forward ones.
+// * The g words carry the voxel kind in the sign and NaN-ness of the float
+//   (free: +g, seed: -g, absent: NaN; g >= 0 always), so a weight is
+//   |g_a| - |g_b| -> exp -> floor at w_min with a NaN-propagating max -> NaN
+//   to 0: no mask logic per edge.
+// * u and p vanish on every non-free voxel, so p_k = u + beta p needs no mask.
 // * The operator is applied in difference form, sum_j w_ij (p_i - p_j).
 // * delta = (u', A u') is summed over the edges each voxel owns (+x, +y, +z),
 //   one plane behind the stencil, from u' of the neighbours.
-// * One barrier per plane.  Loads are 16-byte cp.async copies into a ring of
-//   NR = D + 2 planes, issued D planes ahead.
+// * One barrier per plane; the z loop is unrolled by two (z-chunks start at
+//   even planes) so the exchange buffers have static parity.  Loads are
+//   16-byte cp.async copies into a ring of NR = D + 2 planes, D planes ahead.
 //
 // Tile: TX x TY interior voxels (TX a multiple of 4).  The thread grid covers
 // strips x = -4 .. TX+3 (SX = TX/4 + 2 strips) and rows y = -1 .. TY+1
 // (RY = TY + 3 rows): p_k is needed on x = -1 .. TX+1, y = -1 .. TY+1; u' on
 // x = 0 .. TX, y = 0 .. TY (the +x / +y ends of the owned edges).  This needs
 // the padded layout with an x margin of 4 voxels (the first strip of a tile
-// starts 16-byte aligned) and y / z margins of 2.
+// starts 16-byte aligned) and y / z margins of 2, margins absent (NaN).
 #pragma once
+
+#include <type_traits>
 
 #include "rw_internal.h"
 #include "sweep4_kernel.cuh"
@@ -41,9 +49,9 @@ struct Strip {
     static constexpr int PS = RY * SX;          // strips per plane
     static constexpr int NR = D + 2;            // ring planes
     static constexpr int NI = TX * TY;          // interior voxels
-    // words: ring (u, p, g|code; NR planes), delta ring (interior), exchange
-    // planes (p_k, forward x and y weights, u'; 2 each), strip-end arrays
-    // (first p_k, last p_k, last forward x weight, first u'; 2 each)
+    // words: ring (u, p, g; NR planes), delta ring (interior), exchange planes
+    // (p_k, forward x and y weights, u'; 2 each), strip-end arrays (first
+    // p_k, last p_k, last forward x weight, first u'; 2 each)
     static constexpr size_t words = (size_t)3 * NR * PL + (size_t)NR * NI + (size_t)4 * 2 * PL + (size_t)4 * 2 * PS;
     static constexpr size_t bytes = words * 4;
 };
@@ -55,17 +63,32 @@ constexpr size_t sweep5_smem_bytes() {
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ uint4 lds4u(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
-__device__ __forceinline__ void sts4(float* p, float a, float b, float c, float d) {
-    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+__device__ __forceinline__ void sts4(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
-__device__ __forceinline__ void stg4(float* p, float a, float b, float c, float d) {
-    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+
+// Edge weight max(exp(-beta (g_a - g_b)^2), w_min) from two signed g words;
+// 0 when either voxel is absent (NaN).
+__device__ __forceinline__ float wgt5(uint32_t a, uint32_t b, float c2, float wmin) {
+    const float d = fabsf(__uint_as_float(a)) - fabsf(__uint_as_float(b));
+    const float e = ex2_approx(c2 * d * d);
+    float w;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(w) : "f"(e), "f"(wmin));
+    return fmaxf(w, 0.0f);
 }
+
+// Per-strip registers carried from one plane to the next.
+struct StripState {
+    float pkm[4];   // p_k(z-1)
+    float pk0[4];   // p_k(z)
+    uint32_t g0[4]; // g word(z)
+    float wzm[4];   // w(z-1, z)
+};
 
 template <int TX, int TY, int NT, int D, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
     using L = Strip<TX, TY, D>;
-    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR;
+    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR, NI = L::NI;
     static_assert(TX % 4 == 0, "tile width");
     static_assert(SX * RY <= NT, "threads");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -73,7 +96,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
     float* rP = rU + NR * PL;                                    // [NR][RY][WS]
     uint32_t* rG = reinterpret_cast<uint32_t*>(rP + NR * PL);   // [NR][RY][WS]
     float* rX = reinterpret_cast<float*>(rG + NR * PL);         // [NR][TY][TX]
-    float* ePK = rX + NR * L::NI;                                // [2][RY][WS]
+    float* ePK = rX + NR * NI;                                   // [2][RY][WS]
     float* eWY = ePK + 2 * PL;                                   // [2][RY][WS]
     float* eWX4 = eWY + 2 * PL;                                  // [2][RY][WS]
     float* eUN = eWX4 + 2 * PL;                                  // [2][RY][WS]
@@ -88,13 +111,13 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
     const int sx = tid % SX, ry = tid / SX;
     const bool live = ry < RY;
     const int y = ry - 1;
-    const bool sten = live && y >= 0 && y <= TY && sx >= 1;              // computes u' (x = 0..TX+3)
+    const bool sten = live && y >= 0 && y <= TY && sx >= 1;                  // computes u' (x = 0..TX+3)
     const bool inner = live && y >= 0 && y < TY && sx >= 1 && sx <= TX / 4;  // owns output voxels
     const bool has_right = sx + 1 < SX;
     const bool has_down = ry + 1 < RY;
-    const int wofs = ry * WS + 4 * sx;      // this strip in a plane
-    const int sofs = ry * SX + sx;          // this strip in a strip array
-    const int xofs = (y * TX + 4 * (sx - 1));  // this strip in the delta ring (inner only)
+    const int wofs = ry * WS + 4 * sx;         // this strip in a plane
+    const int sofs = ry * SX + sx;             // this strip in a strip array
+    const int xofs = y * TX + 4 * (sx - 1);    // this strip in the delta ring (inner only)
 
     const int tpb = A.ntx * A.nty * A.nzc;
     const int64_t nwork = (int64_t)(A.list ? *A.nlist : A.bx.nbox) * tpb;
@@ -111,11 +134,13 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
         BoxScalars* S = A.sc + box;
         if (!S->active) continue;
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
-        const float alpha = (float)S->alpha, bcg = (float)S->beta;
+        const float alpha = (float)S->alpha;
+        // p_k = ku u + bp p: u + beta p, or p itself when the direction is kept
         const bool keep = S->phase == 2;
+        const float ku = keep ? 0.0f : 1.0f, bp = keep ? 1.0f : (float)S->beta;
         int ez = A.bx.nz;
         if (A.bx.ext) ez = A.bx.ext[3 * box + 2];
-        const int z0 = tz * A.zc;
+        const int z0 = tz * A.zc;  // even: the chunk depth is even
         const int z1 = min(z0 + A.zc, ez);
         float a_gam = 0.f, a_rr = 0.f, a_del = 0.f, a_eps = 0.f, a_pi = 0.f, a_tau = 0.f;
         if (z0 < ez) {
@@ -137,29 +162,17 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 cp_async16(s_base + (uint32_t)(NR * PL * 4) + so, Pb + pz);
                 cp_async16(s_base + (uint32_t)(2 * NR * PL * 4) + so, Gb + pz);
                 if (inner && z >= z0 && z < z1)
-                    cp_async16(s_base + (uint32_t)((3 * NR * PL + slot(z) * L::NI + xofs) * 4), Xb + pz);
+                    cp_async16(s_base + (uint32_t)((3 * NR * PL + slot(z) * NI + xofs) * 4), Xb + pz);
             };
 
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                if (z0 - 1 + d <= z1 + 1) issue(z0 - 1 + d);
-                cp_async_commit();
-            }
-            // registers of this strip (see the step below for their planes)
-            float pkm[4] = {0, 0, 0, 0}, pk0[4] = {0, 0, 0, 0};
-            uint32_t g0[4] = {0u, 0u, 0u, 0u};
-            float wzm[4] = {0, 0, 0, 0};
-
-            // step z: at entry pk0 = p_k(z), pkm = p_k(z-1), g0 = g|code(z),
-            // wzm = w(z-1, z).  The strip's forward x / y weights of plane z
-            // and u'(z-1) are read back from its own slots of the exchange
-            // planes (only this thread writes them).
-            for (int z = z0 - 2; z <= z1; ++z) {
+            // One plane step.  At entry `in` holds the strip's registers for
+            // plane z; `out` receives those for plane z+1.  BC = z & 1.
+            auto step = [&](const int z, const StripState& in, StripState& out, auto bcc) {
+                constexpr int BC = decltype(bcc)::value, BN = BC ^ 1;
                 cp_async_wait<D - 1>();
                 __syncthreads();
                 if (z + 1 + D <= z1 + 1) issue(z + 1 + D);
                 cp_async_commit();
-                const int bn = (z + 1) & 1, bc = z & 1;
                 const int sn = slot(z + 1);
 
                 // -- 1: plane z+1 enters: p_k and the z edge (z, z+1)
@@ -169,20 +182,19 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                     const float4 u4 = lds4(rU + sn * PL + wofs);
                     const float4 p4 = lds4(rP + sn * PL + wofs);
                     const uint4 g4 = lds4u(rG + sn * PL + wofs);
-                    const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, pp[4] = {p4.x, p4.y, p4.z, p4.w};
+                    pkn[0] = fmaf(bp, p4.x, ku * u4.x);
+                    pkn[1] = fmaf(bp, p4.y, ku * u4.y);
+                    pkn[2] = fmaf(bp, p4.z, ku * u4.z);
+                    pkn[3] = fmaf(bp, p4.w, ku * u4.w);
                     gn[0] = g4.x;
                     gn[1] = g4.y;
                     gn[2] = g4.z;
                     gn[3] = g4.w;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const bool fr = (gn[i] & 3u) == 1u;
-                        pkn[i] = keep ? pp[i] : (fr ? fmaf(bcg, pp[i], uu[i]) : 0.0f);
-                        wz0[i] = wgt(g0[i], gn[i], c2, wmin);
-                    }
-                    sts4(ePK + bn * PL + wofs, pkn[0], pkn[1], pkn[2], pkn[3]);
-                    ePF[bn * PS + sofs] = pkn[0];
-                    ePL[bn * PS + sofs] = pkn[3];
+                    for (int i = 0; i < 4; ++i) wz0[i] = wgt5(in.g0[i], gn[i], c2, wmin);
+                    sts4(ePK + BN * PL + wofs, pkn);
+                    ePF[BN * PS + sofs] = pkn[0];
+                    ePL[BN * PS + sofs] = pkn[3];
                 }
 
                 // -- 2: stencil and update at plane z
@@ -190,40 +202,42 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 if (sten && z >= z0) {
                     const float4 uk = lds4(rU + slot(z) * PL + wofs);
                     const float uu[4] = {uk.x, uk.y, uk.z, uk.w};
-                    const float pl = ePL[bc * PS + sofs - 1];
-                    const float pr = has_right ? ePF[bc * PS + sofs + 1] : 0.0f;
-                    const float wl = eWX[bc * PS + sofs - 1];
-                    const float4 pu = lds4(ePK + bc * PL + wofs - WS);
-                    const float4 pd = lds4(ePK + bc * PL + wofs + WS);
-                    const float4 wu = lds4(eWY + bc * PL + wofs - WS);
-                    const float4 wyo = lds4(eWY + bc * PL + wofs);
-                    const float4 wxo = lds4(eWX4 + bc * PL + wofs);
+                    const float pl = ePL[BC * PS + sofs - 1];
+                    const float pr = has_right ? ePF[BC * PS + sofs + 1] : 0.0f;
+                    const float wl = eWX[BC * PS + sofs - 1];
+                    const float4 pu = lds4(ePK + BC * PL + wofs - WS);
+                    const float4 pd = lds4(ePK + BC * PL + wofs + WS);
+                    const float4 wu = lds4(eWY + BC * PL + wofs - WS);
+                    const float4 wyo = lds4(eWY + BC * PL + wofs);
+                    const float4 wxo = lds4(eWX4 + BC * PL + wofs);
                     const float puu[4] = {pu.x, pu.y, pu.z, pu.w}, pdd[4] = {pd.x, pd.y, pd.z, pd.w};
                     const float wuu[4] = {wu.x, wu.y, wu.z, wu.w};
                     const float wy0[4] = {wyo.x, wyo.y, wyo.z, wyo.w}, wx0[4] = {wxo.x, wxo.y, wxo.z, wxo.w};
                     float sv[4], dv[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const float p0 = pk0[i];
+                        const float p0 = in.pk0[i];
                         const float wL = i == 0 ? wl : wx0[i - 1], wR = wx0[i];
-                        const float pL = i == 0 ? pl : pk0[i - 1], pR = i == 3 ? pr : pk0[i + 1];
-                        dv[i] = ((wL + wR) + (wuu[i] + wy0[i])) + (wzm[i] + wz0[i]);
+                        const float pL = i == 0 ? pl : in.pk0[i - 1], pR = i == 3 ? pr : in.pk0[i + 1];
+                        dv[i] = ((wL + wR) + (wuu[i] + wy0[i])) + (in.wzm[i] + wz0[i]);
                         // difference form: the weak edges of a strongly linked
                         // voxel keep their relative precision
                         sv[i] = ((wL * (p0 - pL) + wR * (p0 - pR)) + (wuu[i] * (p0 - puu[i]) + wy0[i] * (p0 - pdd[i]))) +
-                                (wzm[i] * (p0 - pkm[i]) + wz0[i] * (p0 - pkn[i]));
-                        const bool isfree = (g0[i] & 3u) == 1u && dv[i] > 0.0f;
+                                (in.wzm[i] * (p0 - in.pkm[i]) + wz0[i] * (p0 - pkn[i]));
+                        // free voxels carry +g (sign bit clear)
+                        const bool isfree = (int)in.g0[i] >= 0 && dv[i] > 0.0f;
                         un0[i] = isfree ? uu[i] - alpha * sv[i] * __fdividef(1.0f, dv[i]) : 0.0f;
                     }
-                    sts4(eUN + bc * PL + wofs, un0[0], un0[1], un0[2], un0[3]);
-                    eUF[bc * PS + sofs] = un0[0];
+                    sts4(eUN + BC * PL + wofs, un0);
+                    eUF[BC * PS + sofs] = un0[0];
                     if (inner && z < z1) {
                         const int64_t pz = (int64_t)(z + 2) * plane;
-                        const float4 xs = lds4(rX + slot(z) * L::NI + xofs);
-                        stg4(Uo + pz, un0[0], un0[1], un0[2], un0[3]);
-                        stg4(Po + pz, pk0[0], pk0[1], pk0[2], pk0[3]);
-                        stg4(Xb + pz, fmaf(alpha, pk0[0], xs.x), fmaf(alpha, pk0[1], xs.y), fmaf(alpha, pk0[2], xs.z),
-                             fmaf(alpha, pk0[3], xs.w));
+                        const float4 xs = lds4(rX + slot(z) * NI + xofs);
+                        const float xn[4] = {fmaf(alpha, in.pk0[0], xs.x), fmaf(alpha, in.pk0[1], xs.y),
+                                             fmaf(alpha, in.pk0[2], xs.z), fmaf(alpha, in.pk0[3], xs.w)};
+                        sts4(Uo + pz, un0);
+                        sts4(Po + pz, in.pk0);
+                        sts4(Xb + pz, xn);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             // p_k and u' vanish on non-free voxels
@@ -231,20 +245,19 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                             a_gam = fmaf(du, un0[i], a_gam);
                             a_rr = fmaf(du, du, a_rr);
                             a_eps = fmaf(un0[i], sv[i], a_eps);
-                            a_pi = fmaf(pk0[i], sv[i], a_pi);
-                            a_tau = fmaf(du, pk0[i], a_tau);
+                            a_pi = fmaf(in.pk0[i], sv[i], a_pi);
+                            a_tau = fmaf(du, in.pk0[i], a_tau);
                         }
                     }
                 }
 
                 // -- 3: delta over the edges owned by plane z-1 (+x, +y, +z)
                 if (inner && z - 1 >= z0) {
-                    const int bp = bn;  // (z - 1) & 1
-                    const float ur = eUF[bp * PS + sofs + 1];
-                    const float4 ud = lds4(eUN + bp * PL + wofs + WS);
-                    const float4 um = lds4(eUN + bp * PL + wofs);
-                    const float4 wxv = lds4(eWX4 + bp * PL + wofs);
-                    const float4 wyv = lds4(eWY + bp * PL + wofs);
+                    const float ur = eUF[BN * PS + sofs + 1];
+                    const float4 ud = lds4(eUN + BN * PL + wofs + WS);
+                    const float4 um = lds4(eUN + BN * PL + wofs);
+                    const float4 wxv = lds4(eWX4 + BN * PL + wofs);
+                    const float4 wyv = lds4(eWY + BN * PL + wofs);
                     const float udd[4] = {ud.x, ud.y, ud.z, ud.w}, unm[4] = {um.x, um.y, um.z, um.w};
                     const float wxm[4] = {wxv.x, wxv.y, wxv.z, wxv.w}, wym[4] = {wyv.x, wyv.y, wyv.z, wyv.w};
 #pragma unroll
@@ -254,34 +267,53 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                         const float dz = unm[i] - un0[i];
                         a_del = fmaf(wxm[i] * dx, dx, a_del);
                         a_del = fmaf(wym[i] * dy, dy, a_del);
-                        a_del = fmaf(wzm[i] * dz, dz, a_del);
+                        a_del = fmaf(in.wzm[i] * dz, dz, a_del);
                     }
                 }
 
                 // -- 4: forward x / y weights of plane z+1 (into the slots plane
-                // z-1 used: its last reader was step 3 of this thread)
+                // z-1 used: their last reader was step 3 of this thread)
                 if (live) {
-                    const uint32_t gr = has_right ? rG[sn * PL + wofs + 4] : 0u;
-                    const uint4 gd = has_down ? lds4u(rG + sn * PL + wofs + WS) : make_uint4(0u, 0u, 0u, 0u);
+                    const uint32_t gr = has_right ? rG[sn * PL + wofs + 4] : 0xffc00000u;
+                    const uint4 gd = has_down ? lds4u(rG + sn * PL + wofs + WS)
+                                              : make_uint4(0xffc00000u, 0xffc00000u, 0xffc00000u, 0xffc00000u);
                     const uint32_t gdd[4] = {gd.x, gd.y, gd.z, gd.w};
                     float wxn[4], wyn[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        wxn[i] = wgt(gn[i], i < 3 ? gn[i + 1] : gr, c2, wmin);
-                        wyn[i] = wgt(gn[i], gdd[i], c2, wmin);
+                        wxn[i] = wgt5(gn[i], i < 3 ? gn[i + 1] : gr, c2, wmin);
+                        wyn[i] = wgt5(gn[i], gdd[i], c2, wmin);
                     }
-                    sts4(eWY + bn * PL + wofs, wyn[0], wyn[1], wyn[2], wyn[3]);
-                    sts4(eWX4 + bn * PL + wofs, wxn[0], wxn[1], wxn[2], wxn[3]);
-                    eWX[bn * PS + sofs] = wxn[3];
+                    sts4(eWY + BN * PL + wofs, wyn);
+                    sts4(eWX4 + BN * PL + wofs, wxn);
+                    eWX[BN * PS + sofs] = wxn[3];
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    pkm[i] = pk0[i];
-                    pk0[i] = pkn[i];
-                    g0[i] = gn[i];
-                    wzm[i] = wz0[i];
+                    out.pkm[i] = in.pk0[i];
+                    out.pk0[i] = pkn[i];
+                    out.g0[i] = gn[i];
+                    out.wzm[i] = wz0[i];
                 }
+            };
+
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                if (z0 - 1 + d <= z1 + 1) issue(z0 - 1 + d);
+                cp_async_commit();
             }
+            StripState sa, sb;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                sa.pkm[i] = sa.pk0[i] = sa.wzm[i] = 0.0f;
+                sa.g0[i] = 0xffc00000u;  // plane z0-2 is never used: absent
+            }
+            int z = z0 - 2;
+            for (; z + 1 <= z1; z += 2) {
+                step(z, sa, sb, std::integral_constant<int, 0>());
+                step(z + 1, sb, sa, std::integral_constant<int, 1>());
+            }
+            if (z <= z1) step(z, sa, sb, std::integral_constant<int, 0>());
             cp_async_wait<0>();
         }
         const float fv[6] = {a_gam, a_rr, a_del, a_eps, a_pi, a_tau};
