@@ -248,6 +248,8 @@ def run(args):
                        "precision": "FP32 vectors/stencil, FP64 reductions + FP64-residual refinement",
                        "tol": TOL, "iters_per_solve": stats[0]["iters"], "refine_rounds": stats[0]["refine_rounds"],
                        "rel_resid": stats[0]["rel_resid"], "replicas": ws,
+                       "tile": {v: k for k, v in rw._abi.RW_TILE.items()}.get(stats[0]["tile"], stats[0]["tile"]),
+                       "sweeps_per_graph": stats[0]["iters_per_graph"],
                        "l2": "inputs larger than L2 (about 470 MB streamed per sweep), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,

@@ -125,7 +125,9 @@ enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, 
        RW_TILE_P40x8 = 18, RW_TILE_P32x20 = 19,
        /* register-blocked strips of 4 voxels (padded layout, x margin 4) */
        RW_TILE_S64x11 = 20, RW_TILE_S32x22 = 21, RW_TILE_S32x20 = 22, RW_TILE_S64x8 = 23,
-       RW_TILE_S40x20 = 24, RW_TILE_S40x8 = 25 };
+       RW_TILE_S40x20 = 24, RW_TILE_S40x8 = 25,
+       /* register-blocked strips of 2 voxels (padded layout, x margin 2) */
+       RW_TILE_T32x20 = 26, RW_TILE_T64x11 = 27, RW_TILE_T32x12 = 28, RW_TILE_T40x20 = 29, RW_TILE_T40x8 = 30 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */

@@ -447,7 +447,7 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     if (!fp64 && ps->cands[0] >= TILE_PADDED_FIRST) {
         // padded box: covers whole tiles of every candidate; margins of 2
         // voxels (x: 4 for the strip kernel, whose tiles start 16-byte aligned)
-        const int mx = ps->cands[0] >= TILE_STRIP_FIRST ? 4 : 2;
+        const int mx = tile_margin(ps->cands[0]);
         int px = 0, py = 0;
         for (int t : ps->cands) {
             int tx, ty;
@@ -593,7 +593,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     if (!cur64) {
         RCK(ws_get_t(w, S_GC, ps.nvec * 4, &gc));
         // the strip kernel's format marks absent voxels (margins included) NaN
-        const int fmt = ps.pad.mx == 4 ? 1 : 0;
+        const int fmt = ps.cands[0] >= TILE_STRIP_FIRST ? 1 : 0;
         if (fmt) CK(counted(launch_fill_u32(gc, ps.nvec, GC_ABSENT, w->stream)));
         else if (ps.pad.px) CK(cudaMemsetAsync(gc, 0, ps.nvec * 4, w->stream));
         CK(counted(launch_pack_gc(bx, ps.pad, P.g, P.gtype, P.code, gc, w->stream, fmt)));

@@ -5,31 +5,36 @@ namespace rwk {
 
 namespace {
 
-// tile id -> (TX, TY, threads, planes ahead, minimum resident CTAs)
-#define RW_STRIP_TILES(X)      \
-    X(20, 64, 11, 256, 2, 2)   \
-    X(21, 32, 22, 256, 2, 2)   \
-    X(22, 32, 20, 256, 2, 2)   \
-    X(23, 64, 8, 224, 2, 2)    \
-    X(24, 40, 20, 288, 2, 2)   \
-    X(25, 40, 8, 160, 2, 3)
+// tile id -> (TX, TY, voxels per strip, threads, planes ahead, minimum resident CTAs)
+#define RW_STRIP_TILES(X)         \
+    X(20, 64, 11, 4, 256, 2, 2)   \
+    X(21, 32, 22, 4, 256, 2, 2)   \
+    X(22, 32, 20, 4, 256, 2, 2)   \
+    X(23, 64, 8, 4, 224, 2, 2)    \
+    X(24, 40, 20, 4, 288, 2, 2)   \
+    X(25, 40, 8, 4, 160, 2, 3)    \
+    X(26, 32, 20, 2, 416, 2, 2)   \
+    X(27, 64, 11, 2, 480, 2, 2)   \
+    X(28, 32, 12, 2, 288, 2, 3)   \
+    X(29, 40, 20, 2, 512, 2, 2)   \
+    X(30, 40, 8, 2, 256, 2, 4)
 
-template <int TX, int TY, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
-    k_sweep5<TX, TY, NT, D, MB><<<grid, NT, sweep5_smem_bytes<TX, TY, D>(), s>>>(a);
+    k_sweep5<TX, TY, V, NT, D, MB><<<grid, NT, sweep5_smem_bytes<TX, TY, V, D>(), s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TX, int TY, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB>
 cudaError_t prepare_one() {
-    return cudaFuncSetAttribute(k_sweep5<TX, TY, NT, D, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep5_smem_bytes<TX, TY, D>());
+    return cudaFuncSetAttribute(k_sweep5<TX, TY, V, NT, D, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep5_smem_bytes<TX, TY, V, D>());
 }
 
-template <int TX, int TY, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB>
 int occupancy_one() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, NT, D, MB>, NT, sweep5_smem_bytes<TX, TY, D>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, V, NT, D, MB>, NT, sweep5_smem_bytes<TX, TY, V, D>());
     return n;
 }
 
@@ -37,9 +42,9 @@ int occupancy_one() {
 
 cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     switch (tile) {
-#define X(id, tx, ty, nt, d, mb) \
-    case id:                     \
-        return launch_one<tx, ty, nt, d, mb>(a, grid, s);
+#define X(id, tx, ty, v, nt, d, mb) \
+    case id:                        \
+        return launch_one<tx, ty, v, nt, d, mb>(a, grid, s);
         RW_STRIP_TILES(X)
 #undef X
     default:
@@ -49,9 +54,9 @@ cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s
 
 cudaError_t sweep5_prepare(int tile) {
     switch (tile) {
-#define X(id, tx, ty, nt, d, mb) \
-    case id:                     \
-        return prepare_one<tx, ty, nt, d, mb>();
+#define X(id, tx, ty, v, nt, d, mb) \
+    case id:                        \
+        return prepare_one<tx, ty, v, nt, d, mb>();
         RW_STRIP_TILES(X)
 #undef X
     default:
@@ -61,9 +66,9 @@ cudaError_t sweep5_prepare(int tile) {
 
 int sweep5_occupancy(int tile) {
     switch (tile) {
-#define X(id, tx, ty, nt, d, mb) \
-    case id:                     \
-        return occupancy_one<tx, ty, nt, d, mb>();
+#define X(id, tx, ty, v, nt, d, mb) \
+    case id:                        \
+        return occupancy_one<tx, ty, v, nt, d, mb>();
         RW_STRIP_TILES(X)
 #undef X
     default:
@@ -73,9 +78,9 @@ int sweep5_occupancy(int tile) {
 
 size_t sweep5_smem(int tile) {
     switch (tile) {
-#define X(id, tx, ty, nt, d, mb) \
-    case id:                     \
-        return sweep5_smem_bytes<tx, ty, d>();
+#define X(id, tx, ty, v, nt, d, mb) \
+    case id:                        \
+        return sweep5_smem_bytes<tx, ty, v, d>();
         RW_STRIP_TILES(X)
 #undef X
     default:

@@ -4,11 +4,12 @@
 // A-conjugation, u = D^-1 r stored, weights recomputed from g every sweep,
 // six inner products), organised to spend few instructions per voxel:
 //
-// * A thread owns a strip of four consecutive voxels of one row of the tile
-//   (one 16-byte word of every streamed vector) and marches it through z.
+// * A thread owns a strip of V (4 or 2) consecutive voxels of one row of the
+//   tile (one 16- or 8-byte word of every streamed vector) and marches it
+//   through z.
 //   The strip's own values at z-1, z, z+1 (p_k, the g words, the z-edge
 //   weights) stay in registers; only x/y neighbours are exchanged, through
-//   double-buffered shared planes read with 128-bit loads (the strip ends
+//   double-buffered shared planes read with vector loads (the strip ends
 //   through small per-strip arrays).
 // * Every edge weight is evaluated once per plane, by the voxel that owns the
 //   edge as its forward (+x, +y, +z) edge; the backward weights of a voxel
@@ -23,14 +24,14 @@
 //   one plane behind the stencil, from u' of the neighbours.
 // * One barrier per plane; the z loop is unrolled by two (z-chunks start at
 //   even planes) so the exchange buffers have static parity.  Loads are
-//   16-byte cp.async copies into a ring of NR = D + 2 planes, D planes ahead.
+//   4V-byte cp.async copies into a ring of NR = D + 2 planes, D planes ahead.
 //
-// Tile: TX x TY interior voxels (TX a multiple of 4).  The thread grid covers
-// strips x = -4 .. TX+3 (SX = TX/4 + 2 strips) and rows y = -1 .. TY+1
+// Tile: TX x TY interior voxels (TX a multiple of V).  The thread grid covers
+// strips x = -V .. TX+V-1 (SX = TX/V + 2 strips) and rows y = -1 .. TY+1
 // (RY = TY + 3 rows): p_k is needed on x = -1 .. TX+1, y = -1 .. TY+1; u' on
 // x = 0 .. TX, y = 0 .. TY (the +x / +y ends of the owned edges).  This needs
-// the padded layout with an x margin of 4 voxels (the first strip of a tile
-// starts 16-byte aligned) and y / z margins of 2, margins absent (NaN).
+// the padded layout with an x margin of V voxels (the first strip of a tile
+// starts 4V-byte aligned) and y / z margins of 2, margins absent (NaN).
 #pragma once
 
 #include <type_traits>
@@ -40,11 +41,11 @@
 
 namespace rwk {
 
-template <int TX, int TY, int D>
+template <int TX, int TY, int V, int D>
 struct Strip {
-    static constexpr int SX = TX / 4 + 2;       // strips per row (one 4-voxel halo strip each side)
+    static constexpr int SX = TX / V + 2;       // strips per row (one halo strip each side)
     static constexpr int RY = TY + 3;           // rows y = -1 .. TY+1
-    static constexpr int WS = TX + 8;           // words per row
+    static constexpr int WS = TX + 2 * V;       // words per row
     static constexpr int PL = RY * WS;          // words per plane
     static constexpr int PS = RY * SX;          // strips per plane
     static constexpr int NR = D + 2;            // ring planes
@@ -56,15 +57,41 @@ struct Strip {
     static constexpr size_t bytes = words * 4;
 };
 
-template <int TX, int TY, int D>
+template <int TX, int TY, int V, int D>
 constexpr size_t sweep5_smem_bytes() {
-    return Strip<TX, TY, D>::bytes;
+    return Strip<TX, TY, V, D>::bytes;
 }
 
-__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ uint4 lds4u(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
-__device__ __forceinline__ void sts4(float* p, const float* v) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+// V-wide vector loads / stores (V = 4: 128-bit, V = 2: 64-bit).
+template <int V>
+__device__ __forceinline__ void ldv(const float* p, float* v) {
+    if constexpr (V == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    } else {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        v[0] = a.x, v[1] = a.y;
+    }
+}
+template <int V>
+__device__ __forceinline__ void ldv(const uint32_t* p, uint32_t* v) {
+    if constexpr (V == 4) {
+        const uint4 a = *reinterpret_cast<const uint4*>(p);
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    } else {
+        const uint2 a = *reinterpret_cast<const uint2*>(p);
+        v[0] = a.x, v[1] = a.y;
+    }
+}
+template <int V>
+__device__ __forceinline__ void stv(float* p, const float* v) {
+    if constexpr (V == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+template <int V>
+__device__ __forceinline__ void cp_async_v(uint32_t saddr, const void* gmem) {
+    if constexpr (V == 4) cp_async16(saddr, gmem);
+    else cp_async8(saddr, gmem);
 }
 
 // Edge weight max(exp(-beta (g_a - g_b)^2), w_min) from two signed g words;
@@ -78,18 +105,20 @@ __device__ __forceinline__ float wgt5(uint32_t a, uint32_t b, float c2, float wm
 }
 
 // Per-strip registers carried from one plane to the next.
+template <int V>
 struct StripState {
-    float pkm[4];   // p_k(z-1)
-    float pk0[4];   // p_k(z)
-    uint32_t g0[4]; // g word(z)
-    float wzm[4];   // w(z-1, z)
+    float pkm[V];   // p_k(z-1)
+    float pk0[V];   // p_k(z)
+    uint32_t g0[V]; // g word(z)
+    float wzm[V];   // w(z-1, z)
 };
 
-template <int TX, int TY, int NT, int D, int MINB>
+template <int TX, int TY, int V, int NT, int D, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
-    using L = Strip<TX, TY, D>;
+    using L = Strip<TX, TY, V, D>;
     constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR, NI = L::NI;
-    static_assert(TX % 4 == 0, "tile width");
+    static_assert(V == 2 || V == 4, "strip width");
+    static_assert(TX % V == 0, "tile width");
     static_assert(SX * RY <= NT, "threads");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* rU = reinterpret_cast<float*>(smem_raw);             // [NR][RY][WS]
@@ -107,17 +136,35 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
     __shared__ double red[6 * (NT / 32)];
     __shared__ int s_last;
 
+    // Threads are ordered by role so that warps are homogeneous: first the
+    // strips owning output voxels (rows 0..TY-1, strips 1..TX/V), then the
+    // other strips that compute u' (strip SX-1 of those rows, and row TY),
+    // then the halo (strip 0 of every row; rows -1 and TY+1), then idle.
     const int tid = threadIdx.x;
-    const int sx = tid % SX, ry = tid / SX;
+    constexpr int NX = TX / V, NIN = TY * NX, NSN = TY + NX + 1, NHA = RY + 2 * (SX - 1);
+    int sx, ry;
+    if (tid < NIN) {
+        ry = 1 + tid / NX, sx = 1 + tid % NX;
+    } else if (tid < NIN + NSN) {
+        const int k = tid - NIN;
+        if (k < TY) ry = 1 + k, sx = SX - 1;
+        else ry = TY + 1, sx = 1 + (k - TY);
+    } else if (tid < NIN + NSN + NHA) {
+        const int k = tid - NIN - NSN;
+        if (k < RY) ry = k, sx = 0;
+        else ry = (k - RY) < SX - 1 ? 0 : RY - 1, sx = 1 + (k - RY) % (SX - 1);
+    } else {
+        ry = RY, sx = 0;  // idle
+    }
     const bool live = ry < RY;
     const int y = ry - 1;
-    const bool sten = live && y >= 0 && y <= TY && sx >= 1;                  // computes u' (x = 0..TX+3)
-    const bool inner = live && y >= 0 && y < TY && sx >= 1 && sx <= TX / 4;  // owns output voxels
+    const bool sten = live && y >= 0 && y <= TY && sx >= 1;                  // computes u' (x = 0..TX+V-1)
+    const bool inner = live && y >= 0 && y < TY && sx >= 1 && sx <= TX / V;  // owns output voxels
     const bool has_right = sx + 1 < SX;
     const bool has_down = ry + 1 < RY;
-    const int wofs = ry * WS + 4 * sx;         // this strip in a plane
+    const int wofs = ry * WS + V * sx;         // this strip in a plane
     const int sofs = ry * SX + sx;             // this strip in a strip array
-    const int xofs = y * TX + 4 * (sx - 1);    // this strip in the delta ring (inner only)
+    const int xofs = y * TX + V * (sx - 1);    // this strip in the delta ring (inner only)
 
     const int tpb = A.ntx * A.nty * A.nzc;
     const int64_t nwork = (int64_t)(A.list ? *A.nlist : A.bx.nbox) * tpb;
@@ -144,8 +191,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
         const int z1 = min(z0 + A.zc, ez);
         float a_gam = 0.f, a_rr = 0.f, a_del = 0.f, a_eps = 0.f, a_pi = 0.f, a_tau = 0.f;
         if (z0 < ez) {
-            // padded coordinates of this strip: x + 4, y + 2, z + 2
-            const int64_t base = (int64_t)box * bstride + (int64_t)(ty * TY + ry + 1) * PX + tx * TX + 4 * sx;
+            // padded coordinates of this strip: x + V, y + 2, z + 2
+            const int64_t base = (int64_t)box * bstride + (int64_t)(ty * TY + ry + 1) * PX + tx * TX + V * sx;
             const float* Ub = static_cast<const float*>(A.u_in) + base;
             const float* Pb = static_cast<const float*>(A.p_in) + base;
             const uint32_t* Gb = A.gc + base;
@@ -158,16 +205,16 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 if (!live) return;
                 const int64_t pz = (int64_t)(z + 2) * plane;
                 const uint32_t so = (uint32_t)((slot(z) * PL + wofs) * 4);
-                cp_async16(s_base + so, Ub + pz);
-                cp_async16(s_base + (uint32_t)(NR * PL * 4) + so, Pb + pz);
-                cp_async16(s_base + (uint32_t)(2 * NR * PL * 4) + so, Gb + pz);
+                cp_async_v<V>(s_base + so, Ub + pz);
+                cp_async_v<V>(s_base + (uint32_t)(NR * PL * 4) + so, Pb + pz);
+                cp_async_v<V>(s_base + (uint32_t)(2 * NR * PL * 4) + so, Gb + pz);
                 if (inner && z >= z0 && z < z1)
-                    cp_async16(s_base + (uint32_t)((3 * NR * PL + slot(z) * NI + xofs) * 4), Xb + pz);
+                    cp_async_v<V>(s_base + (uint32_t)((3 * NR * PL + slot(z) * NI + xofs) * 4), Xb + pz);
             };
 
             // One plane step.  At entry `in` holds the strip's registers for
             // plane z; `out` receives those for plane z+1.  BC = z & 1.
-            auto step = [&](const int z, const StripState& in, StripState& out, auto bcc) {
+            auto step = [&](const int z, const StripState<V>& in, StripState<V>& out, auto bcc) {
                 constexpr int BC = decltype(bcc)::value, BN = BC ^ 1;
                 cp_async_wait<D - 1>();
                 __syncthreads();
@@ -176,49 +223,47 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 const int sn = slot(z + 1);
 
                 // -- 1: plane z+1 enters: p_k and the z edge (z, z+1)
-                float pkn[4] = {0, 0, 0, 0}, wz0[4] = {0, 0, 0, 0};
-                uint32_t gn[4] = {0u, 0u, 0u, 0u};
-                if (live) {
-                    const float4 u4 = lds4(rU + sn * PL + wofs);
-                    const float4 p4 = lds4(rP + sn * PL + wofs);
-                    const uint4 g4 = lds4u(rG + sn * PL + wofs);
-                    pkn[0] = fmaf(bp, p4.x, ku * u4.x);
-                    pkn[1] = fmaf(bp, p4.y, ku * u4.y);
-                    pkn[2] = fmaf(bp, p4.z, ku * u4.z);
-                    pkn[3] = fmaf(bp, p4.w, ku * u4.w);
-                    gn[0] = g4.x;
-                    gn[1] = g4.y;
-                    gn[2] = g4.z;
-                    gn[3] = g4.w;
+                float pkn[V], wz0[V];
+                uint32_t gn[V];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) wz0[i] = wgt5(in.g0[i], gn[i], c2, wmin);
-                    sts4(ePK + BN * PL + wofs, pkn);
+                for (int i = 0; i < V; ++i) pkn[i] = wz0[i] = 0.0f, gn[i] = GC_ABSENT;
+                if (live) {
+                    float uu[V], pp[V];
+                    ldv<V>(rU + sn * PL + wofs, uu);
+                    ldv<V>(rP + sn * PL + wofs, pp);
+                    ldv<V>(rG + sn * PL + wofs, gn);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) pkn[i] = fmaf(bp, pp[i], ku * uu[i]);
+                    if (sten) {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) wz0[i] = wgt5(in.g0[i], gn[i], c2, wmin);
+                    }
+                    stv<V>(ePK + BN * PL + wofs, pkn);
                     ePF[BN * PS + sofs] = pkn[0];
-                    ePL[BN * PS + sofs] = pkn[3];
+                    ePL[BN * PS + sofs] = pkn[V - 1];
                 }
 
                 // -- 2: stencil and update at plane z
-                float un0[4] = {0, 0, 0, 0};
+                float un0[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) un0[i] = 0.0f;
                 if (sten && z >= z0) {
-                    const float4 uk = lds4(rU + slot(z) * PL + wofs);
-                    const float uu[4] = {uk.x, uk.y, uk.z, uk.w};
+                    float uu[V], puu[V], pdd[V], wuu[V], wy0[V], wx0[V];
+                    ldv<V>(rU + slot(z) * PL + wofs, uu);
                     const float pl = ePL[BC * PS + sofs - 1];
                     const float pr = has_right ? ePF[BC * PS + sofs + 1] : 0.0f;
                     const float wl = eWX[BC * PS + sofs - 1];
-                    const float4 pu = lds4(ePK + BC * PL + wofs - WS);
-                    const float4 pd = lds4(ePK + BC * PL + wofs + WS);
-                    const float4 wu = lds4(eWY + BC * PL + wofs - WS);
-                    const float4 wyo = lds4(eWY + BC * PL + wofs);
-                    const float4 wxo = lds4(eWX4 + BC * PL + wofs);
-                    const float puu[4] = {pu.x, pu.y, pu.z, pu.w}, pdd[4] = {pd.x, pd.y, pd.z, pd.w};
-                    const float wuu[4] = {wu.x, wu.y, wu.z, wu.w};
-                    const float wy0[4] = {wyo.x, wyo.y, wyo.z, wyo.w}, wx0[4] = {wxo.x, wxo.y, wxo.z, wxo.w};
-                    float sv[4], dv[4];
+                    ldv<V>(ePK + BC * PL + wofs - WS, puu);
+                    ldv<V>(ePK + BC * PL + wofs + WS, pdd);
+                    ldv<V>(eWY + BC * PL + wofs - WS, wuu);
+                    ldv<V>(eWY + BC * PL + wofs, wy0);
+                    ldv<V>(eWX4 + BC * PL + wofs, wx0);
+                    float sv[V], dv[V];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < V; ++i) {
                         const float p0 = in.pk0[i];
                         const float wL = i == 0 ? wl : wx0[i - 1], wR = wx0[i];
-                        const float pL = i == 0 ? pl : in.pk0[i - 1], pR = i == 3 ? pr : in.pk0[i + 1];
+                        const float pL = i == 0 ? pl : in.pk0[i - 1], pR = i == V - 1 ? pr : in.pk0[i + 1];
                         dv[i] = ((wL + wR) + (wuu[i] + wy0[i])) + (in.wzm[i] + wz0[i]);
                         // difference form: the weak edges of a strongly linked
                         // voxel keep their relative precision
@@ -228,18 +273,19 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                         const bool isfree = (int)in.g0[i] >= 0 && dv[i] > 0.0f;
                         un0[i] = isfree ? uu[i] - alpha * sv[i] * __fdividef(1.0f, dv[i]) : 0.0f;
                     }
-                    sts4(eUN + BC * PL + wofs, un0);
+                    stv<V>(eUN + BC * PL + wofs, un0);
                     eUF[BC * PS + sofs] = un0[0];
                     if (inner && z < z1) {
                         const int64_t pz = (int64_t)(z + 2) * plane;
-                        const float4 xs = lds4(rX + slot(z) * NI + xofs);
-                        const float xn[4] = {fmaf(alpha, in.pk0[0], xs.x), fmaf(alpha, in.pk0[1], xs.y),
-                                             fmaf(alpha, in.pk0[2], xs.z), fmaf(alpha, in.pk0[3], xs.w)};
-                        sts4(Uo + pz, un0);
-                        sts4(Po + pz, in.pk0);
-                        sts4(Xb + pz, xn);
+                        float xn[V];
+                        ldv<V>(rX + slot(z) * NI + xofs, xn);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
+                        for (int i = 0; i < V; ++i) xn[i] = fmaf(alpha, in.pk0[i], xn[i]);
+                        stv<V>(Uo + pz, un0);
+                        stv<V>(Po + pz, in.pk0);
+                        stv<V>(Xb + pz, xn);
+#pragma unroll
+                        for (int i = 0; i < V; ++i) {
                             // p_k and u' vanish on non-free voxels
                             const float du = dv[i] * un0[i];
                             a_gam = fmaf(du, un0[i], a_gam);
@@ -254,15 +300,14 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 // -- 3: delta over the edges owned by plane z-1 (+x, +y, +z)
                 if (inner && z - 1 >= z0) {
                     const float ur = eUF[BN * PS + sofs + 1];
-                    const float4 ud = lds4(eUN + BN * PL + wofs + WS);
-                    const float4 um = lds4(eUN + BN * PL + wofs);
-                    const float4 wxv = lds4(eWX4 + BN * PL + wofs);
-                    const float4 wyv = lds4(eWY + BN * PL + wofs);
-                    const float udd[4] = {ud.x, ud.y, ud.z, ud.w}, unm[4] = {um.x, um.y, um.z, um.w};
-                    const float wxm[4] = {wxv.x, wxv.y, wxv.z, wxv.w}, wym[4] = {wyv.x, wyv.y, wyv.z, wyv.w};
+                    float udd[V], unm[V], wxm[V], wym[V];
+                    ldv<V>(eUN + BN * PL + wofs + WS, udd);
+                    ldv<V>(eUN + BN * PL + wofs, unm);
+                    ldv<V>(eWX4 + BN * PL + wofs, wxm);
+                    ldv<V>(eWY + BN * PL + wofs, wym);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float dx = unm[i] - (i < 3 ? unm[i + 1] : ur);
+                    for (int i = 0; i < V; ++i) {
+                        const float dx = unm[i] - (i < V - 1 ? unm[i + 1] : ur);
                         const float dy = unm[i] - udd[i];
                         const float dz = unm[i] - un0[i];
                         a_del = fmaf(wxm[i] * dx, dx, a_del);
@@ -272,24 +317,30 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 }
 
                 // -- 4: forward x / y weights of plane z+1 (into the slots plane
-                // z-1 used: their last reader was step 3 of this thread)
-                if (live) {
-                    const uint32_t gr = has_right ? rG[sn * PL + wofs + 4] : 0xffc00000u;
-                    const uint4 gd = has_down ? lds4u(rG + sn * PL + wofs + WS)
-                                              : make_uint4(0xffc00000u, 0xffc00000u, 0xffc00000u, 0xffc00000u);
-                    const uint32_t gdd[4] = {gd.x, gd.y, gd.z, gd.w};
-                    float wxn[4], wyn[4];
+                // z-1 used: their last reader was step 3 of this thread).  Of
+                // the halo, strip 0 needs its last x weight and row -1 its y
+                // weights; row TY+1 none.
+                if (live && ry < RY - 1) {
+                    const uint32_t gr = has_right ? rG[sn * PL + wofs + V] : GC_ABSENT;
+                    uint32_t gdd[V];
+                    if (has_down) {
+                        ldv<V>(rG + sn * PL + wofs + WS, gdd);
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        wxn[i] = wgt5(gn[i], i < 3 ? gn[i + 1] : gr, c2, wmin);
+                        for (int i = 0; i < V; ++i) gdd[i] = GC_ABSENT;
+                    }
+                    float wxn[V], wyn[V];
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        wxn[i] = wgt5(gn[i], i < V - 1 ? gn[i + 1] : gr, c2, wmin);
                         wyn[i] = wgt5(gn[i], gdd[i], c2, wmin);
                     }
-                    sts4(eWY + BN * PL + wofs, wyn);
-                    sts4(eWX4 + BN * PL + wofs, wxn);
-                    eWX[BN * PS + sofs] = wxn[3];
+                    stv<V>(eWY + BN * PL + wofs, wyn);
+                    stv<V>(eWX4 + BN * PL + wofs, wxn);
+                    eWX[BN * PS + sofs] = wxn[V - 1];
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < V; ++i) {
                     out.pkm[i] = in.pk0[i];
                     out.pk0[i] = pkn[i];
                     out.g0[i] = gn[i];
@@ -302,9 +353,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 if (z0 - 1 + d <= z1 + 1) issue(z0 - 1 + d);
                 cp_async_commit();
             }
-            StripState sa, sb;
+            StripState<V> sa, sb;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < V; ++i) {
                 sa.pkm[i] = sa.pk0[i] = sa.wzm[i] = 0.0f;
                 sa.g0[i] = 0xffc00000u;  // plane z0-2 is never used: absent
             }
