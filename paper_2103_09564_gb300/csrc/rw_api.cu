@@ -68,7 +68,7 @@ double now_ms() {
 enum Slot {
     S_G, S_U0, S_U1, S_P0, S_P1, S_DELTA, S_XHI, S_PART, S_RPART, S_SC, S_NACT, S_VOL, S_CODE, S_VAL, S_X0, S_OUT,
     S_RHS, S_EXT, S_JOBS, S_LAB, S_BFLAGS, S_STATS, S_POOL_G, S_POOL_CODE, S_POOL_X, S_ADJ_PART, S_DBETA, S_DG,
-    S_XF, S_STATUS, S_GC, S_LIST, S_COUNT
+    S_XF, S_STATUS, S_GC, S_LIST, S_W64, S_COUNT
 };
 
 struct DevWorkspace {
@@ -588,6 +588,17 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     ra.blocks_per_box = bpb;
     ra.mbeta = -(double)o.beta;
     ra.wmin = (double)o.w_min;
+
+    // FP64 edge weights once per solve (the residual rounds read them) while
+    // they fit a fixed budget; beyond it the residual evaluates them in place
+    constexpr size_t kW64Budget = (size_t)16 << 30;
+    const size_t w64_bytes = (size_t)nvox * bx.nbox * 3 * sizeof(double);
+    if (w64_bytes <= kW64Budget) {
+        double* w3 = nullptr;
+        RCK(ws_get_t(w, S_W64, w64_bytes, &w3));
+        CK(counted(launch_weights64(ra, w3, w->stream)));
+        ra.w3 = w3;
+    }
 
     uint32_t* gc = nullptr;
     if (!cur64) {

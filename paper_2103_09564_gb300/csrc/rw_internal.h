@@ -118,8 +118,14 @@ struct ResidArgs {
     double* part;          // [nbox][blocks][4]: bb, rr, nseed, nfree
     int blocks_per_box;
     double mbeta, wmin;
+    // optional FP64 forward edge weights (+x, +y, +z planes of nbox*nvox
+    // each, caller layout) from launch_weights64; null: computed in place
+    const double* w3 = nullptr;
 };
 cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s);
+// FP64 edge weights, each edge once (its lower voxel's forward edge), for the
+// residual rounds of one solve: w3 holds 3 * nbox * nvox doubles.
+cudaError_t launch_weights64(const ResidArgs& a, double* w3, cudaStream_t s);
 // fp64 = 0: also clears the FP32 correction vector `delta`.
 cudaError_t launch_residual(int fp64, const ResidArgs& a, float* delta, cudaStream_t s);
 cudaError_t launch_accumulate(const Boxes& bx, const Pad& pad, const uint8_t* code, const float* delta, double* x,

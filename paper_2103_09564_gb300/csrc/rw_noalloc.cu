@@ -183,8 +183,7 @@ extern "C" rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* 
     NCK(cudaMemsetAsync(sc, 0, batch * sizeof(BoxScalars), s));
     NCK(launch_quantize(vol->data, vol->dtype, ntot, vol->lo, vol->hi, vol->normalize, RW_STORE_UNORM16, g, s));
     NCK(launch_pack_gc(bx, Pad{0, 0, 0, 0}, g, G_U16, seeds->code, gc, s));
-    ResidArgs ra;
-    memset(&ra, 0, sizeof(ra));
+    ResidArgs ra{};
     ra.bx = bx;
     ra.g = g;
     ra.gtype = G_U16;

@@ -182,8 +182,15 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                     const int64_t j = base + ((int64_t)nbz[k] * ny + nby[k]) * nx + nbx[k];
                     const uint8_t cj = a.code[j];
                     if (cj == ABSENT) continue;
-                    const double dg = gi - gdbl(a.g, a.gtype, j);
-                    const double w = fmax(exp(a.mbeta * dg * dg), a.wmin);
+                    double w;
+                    if (a.w3) {
+                        // the forward edge of the lower voxel of the pair
+                        const int64_t ntot = (int64_t)a.bx.nbox * nvox;
+                        w = a.w3[(int64_t)(k >> 1) * ntot + ((k & 1) ? i : j)];
+                    } else {
+                        const double dg = gi - gdbl(a.g, a.gtype, j);
+                        w = fmax(exp(a.mbeta * dg * dg), a.wmin);
+                    }
                     const double xj = xh[j];
                     d += w;
                     s += w * (xi - xj);
@@ -222,6 +229,43 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
         for (int k = 0; k < 8; ++k) s += red[threadIdx.x][k];
         a.part[((int64_t)box * a.blocks_per_box + blockIdx.x) * 4 + threadIdx.x] = s;
     }
+}
+
+// Forward FP64 weights of every voxel: the same expression, in the same
+// operand order up to an exact sign, as the residual's own evaluation.
+__global__ void k_weights64(const ResidArgs a, double* w3) {
+    const int box = blockIdx.y;
+    const int nx = a.bx.nx, ny = a.bx.ny, nz = a.bx.nz;
+    const int64_t nvox = (int64_t)nx * ny * nz, ntot = (int64_t)a.bx.nbox * nvox;
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nvox) return;
+    int ex, ey, ez;
+    box_extent(a.bx, box, &ex, &ey, &ez);
+    const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+    const int64_t i = (int64_t)box * nvox + li;
+    double wv[3] = {0.0, 0.0, 0.0};
+    if (x < ex && y < ey && z < ez && a.code[i] != ABSENT) {
+        const double gi = gdbl(a.g, a.gtype, i);
+        const bool in[3] = {x + 1 < ex, y + 1 < ey, z + 1 < ez};
+        const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (!in[k]) continue;
+            const int64_t j = i + st[k];
+            if (a.code[j] == ABSENT) continue;
+            const double dg = gi - gdbl(a.g, a.gtype, j);
+            wv[k] = fmax(exp(a.mbeta * dg * dg), a.wmin);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w3[k * ntot + i] = wv[k];
+}
+
+cudaError_t launch_weights64(const ResidArgs& a, double* w3, cudaStream_t s) {
+    const int64_t nvox = (int64_t)a.bx.nx * a.bx.ny * a.bx.nz;
+    dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)a.bx.nbox);
+    k_weights64<<<grid, 256, 0, s>>>(a, w3);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s) {
