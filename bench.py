@@ -36,6 +36,10 @@ TOL = 1e-8
 # (1 B).  The sweep kernel itself moves 28 B (g and code packed in one word).
 SWEEP_BYTES_PER_VOXEL = 27
 KERNEL_BYTES_PER_VOXEL = 28
+# DRAM bytes of one sweep launch on the 256^3 workload, from an ncu capture of
+# this benchmark (median over the timed step's sweeps); reset to None when the
+# sweep kernel changes until it is captured again
+SWEEP_TRAFFIC_256 = None
 def _workload(n):
     return f"plain random walker, {n}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
 
@@ -252,8 +256,10 @@ def run(args):
                        "sweeps_per_graph": stats[0]["iters_per_graph"],
                        "l2": "inputs larger than L2 (about 470 MB streamed per sweep), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_sweep4 (fused PCG sweep)", "peak_source": src,
+                         "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_256 if N == 256 else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, median over "
+                                           "the timed step's k_sweep5 launches (profiles/k_sweep5_plain256.md)",
+                         "kernel": "k_sweep5 (fused PCG sweep)", "peak_source": src,
                          "algorithmic_bytes_per_launch": alg, "basis": "27 B per free voxel per sweep",
                          "kernel_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL, "launch_ms": t_launch_s * 1e3,
                          "sweeps_per_step": sweeps / args.steps},

@@ -2,6 +2,8 @@
 // device workspace, the PCG driver (refinement rounds, CUDA-graph chunks of
 // fused sweeps, per-system convergence), the adjoint, the LOD pyramid and the
 // hierarchical tree (Sec. IV, Fig. 3 processing scheme, level by level).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -278,6 +280,45 @@ struct SolveResult {
     int fp64_fallback = 0;
 };
 
+// TMA descriptors for a strip-sweep launch: the padded arrays as 3-D tensors
+// [PZ * nbox][PY][PX] of 4-byte words; boxes (TX + 2V) x (TY + 3) x 1 for u, p
+// and the g words, TX (V = 4) or TX + 2V (V = 2) x TY x 1 for delta.
+rw_status strip_maps(int tile, SweepArgs* sa) {
+    if (tile < TILE_STRIP_FIRST) return RW_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return fail(RW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    int tx, ty;
+    tile_dims(tile, &tx, &ty);
+    const int v = tile_margin(tile);
+    const cuuint64_t gdim[3] = {(cuuint64_t)sa->px, (cuuint64_t)sa->py, (cuuint64_t)sa->pz * (cuuint64_t)sa->bx.nbox};
+    const cuuint64_t gstr[2] = {(cuuint64_t)sa->px * 4, (cuuint64_t)sa->px * (cuuint64_t)sa->py * 4};
+    const cuuint32_t box_t[3] = {(cuuint32_t)(tx + 2 * v), (cuuint32_t)(ty + 3), 1u};
+    // delta: the interior for 4-voxel strips, the full strip width for 2-voxel
+    // strips (whose interior does not start 16-byte aligned)
+    const cuuint32_t box_x[3] = {(cuuint32_t)(v == 4 ? tx : tx + 2 * v), (cuuint32_t)ty, 1u};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    auto enc = [&](CUtensorMap* m, const void* ptr, const cuuint32_t* box) {
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr), gdim, gstr, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!enc(&sa->tm.u, sa->u_in, box_t) || !enc(&sa->tm.p, sa->p_in, box_t) || !enc(&sa->tm.g, sa->gc, box_t) ||
+        !enc(&sa->tm.x, sa->x, box_x))
+        return fail(RW_ERR_CUDA, "TMA descriptor encoding failed (tile %d, padded %d x %d x %d)", tile, sa->px, sa->py,
+                    sa->pz);
+    return RW_OK;
+}
+
 // Configuration of a sweep over `nact` compacted systems: the z-splitting is
 // deepened so that the systems still iterating fill the GPU again.
 void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, int sms, size_t part_elems,
@@ -320,7 +361,9 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
             sa.u_out = u[par ^ 1];
             sa.p_out = p[par ^ 1];
             sa.parity = par;
-            cudaError_t e = launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream);
+            rw_status ms = fp64 ? RW_OK : strip_maps(cfg.tile, &sa);
+            cudaError_t e = ms == RW_OK ? launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream)
+                                        : cudaErrorInvalidValue;
             if (e != cudaSuccess && le == cudaSuccess) le = e;
             par ^= 1;
         }
@@ -366,7 +409,8 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
         cudaError_t e = cudaEventRecord(ev0, w->stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(exec, w->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev1, w->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(w->pinned, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(w->pinned, n_active_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
@@ -378,7 +422,11 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
         *ms_dev += ms;
         *sweeps += cfg.ipg;
         g_launches += cfg.ipg;
-        n_act = *w->pinned;
+        n_act = w->pinned[0];
+        if (w->pinned[1]) {
+            st = fail(RW_ERR_CUDA, "PCG sweep: a load wait ran out (tile %d)", cfg.tile);
+            break;
+        }
         if (n_act > 0 && *sweeps < cap) {
             st = compact(n_act);
             if (st != RW_OK) break;
@@ -405,6 +453,7 @@ rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* co
         sa.u_out = u[par ^ 1];
         sa.p_out = p[par ^ 1];
         sa.parity = par;
+        if (!fp64) RCK(strip_maps(cfg.tile, &sa));
         CK(counted(launch_sweep(fp64, gtype, cfg.tile, sa, cfg.grid, w->stream)));
         par ^= 1;
     }
@@ -624,6 +673,8 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     sa.sc = sc;
     sa.partials = part;
     sa.n_active = nact;
+    sa.err = nact + 1;  // the strip sweep's load-wait flag, next to the active count
+    CK(cudaMemsetAsync(nact + 1, 0, sizeof(int), w->stream));
     sa.c2f = (float)(-(double)o.beta * 1.4426950408889634);
     sa.wminf = o.w_min;
     sa.mbeta = -(double)o.beta;

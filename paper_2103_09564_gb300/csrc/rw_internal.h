@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of librw.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,6 +40,12 @@ struct Boxes {
     const int* ext;  // device [nbox][3] (x, y, z) or nullptr = full box
 };
 
+// TMA descriptors of the strip sweep's streamed arrays (u_in, p_in, g words,
+// delta), encoded by the host for the launch's buffers and tile.
+struct StripMaps {
+    CUtensorMap u, p, g, x;
+};
+
 struct SweepArgs {
     Boxes bx;
     int ntx, nty, nzc, zc;  // tiles per box: x, y, z-chunks; chunk depth
@@ -61,6 +68,8 @@ struct SweepArgs {
     float wminf;
     double mbeta;           // -beta, FP64 weights
     double wmin;
+    int* err = nullptr;     // set to 1 by a strip sweep whose load wait ran out
+    StripMaps tm;           // k_sweep5 only
 };
 
 enum GType { G_U16 = 0, G_F32 = 1 };

@@ -23,8 +23,12 @@
 // * delta = (u', A u') is summed over the edges each voxel owns (+x, +y, +z),
 //   one plane behind the stencil, from u' of the neighbours.
 // * One barrier per plane; the z loop is unrolled by two (z-chunks start at
-//   even planes) so the exchange buffers have static parity.  Loads are
-//   4V-byte cp.async copies into a ring of NR = D + 2 planes, D planes ahead.
+//   even planes) so the exchange buffers have static parity.  Loads are TMA
+//   tile copies (cp.async.bulk.tensor, one per array and plane, issued by one
+//   thread) into a ring of NR = D + 2 planes, D planes ahead, completing on
+//   one mbarrier per ring slot.  Every wait is bounded: a wait that runs out
+//   sets the error flag and the thread stops waiting (it still reaches every
+//   barrier, so the CTA finishes).
 //
 // Tile: TX x TY interior voxels (TX a multiple of V).  The thread grid covers
 // strips x = -V .. TX+V-1 (SX = TX/V + 2 strips) and rows y = -1 .. TY+1
@@ -50,10 +54,16 @@ struct Strip {
     static constexpr int PS = RY * SX;          // strips per plane
     static constexpr int NR = D + 2;            // ring planes
     static constexpr int NI = TX * TY;          // interior voxels
+    // delta box: the interior (V = 4: its first column is 16-byte aligned),
+    // or the full strip width from the halo strip (V = 2)
+    static constexpr int XW = V == 4 ? TX : WS, XC = V == 4 ? V : 0;
+    static constexpr int PLA = (PL + 31) & ~31; // ring plane stride (128-byte aligned TMA destinations)
+    static constexpr int NIA = (XW * TY + 31) & ~31;
     // words: ring (u, p, g; NR planes), delta ring (interior), exchange planes
     // (p_k, forward x and y weights, u'; 2 each), strip-end arrays (first
-    // p_k, last p_k, last forward x weight, first u'; 2 each)
-    static constexpr size_t words = (size_t)3 * NR * PL + (size_t)NR * NI + (size_t)4 * 2 * PL + (size_t)4 * 2 * PS;
+    // p_k, last p_k, last forward x weight, first u'; 2 each), alignment slack
+    static constexpr size_t words =
+        (size_t)3 * NR * PLA + (size_t)NR * NIA + (size_t)4 * 2 * PL + (size_t)4 * 2 * PS + 32;
     static constexpr size_t bytes = words * 4;
 };
 
@@ -88,10 +98,34 @@ __device__ __forceinline__ void stv(float* p, const float* v) {
     if constexpr (V == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     else *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
 }
-template <int V>
-__device__ __forceinline__ void cp_async_v(uint32_t saddr, const void* gmem) {
-    if constexpr (V == 4) cp_async16(saddr, gmem);
-    else cp_async8(saddr, gmem);
+// mbarrier and TMA helpers (shared::cta addresses).
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase `parity` of `bar` to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
 }
 
 // Edge weight max(exp(-beta (g_a - g_b)^2), w_min) from two signed g words;
@@ -114,18 +148,27 @@ struct StripState {
 };
 
 template <int TX, int TY, int V, int NT, int D, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
+__global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ SweepArgs A) {
     using L = Strip<TX, TY, V, D>;
-    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR, NI = L::NI;
+    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR;
+    constexpr int PLA = L::PLA, NIA = L::NIA;
     static_assert(V == 2 || V == 4, "strip width");
     static_assert(TX % V == 0, "tile width");
     static_assert(SX * RY <= NT, "threads");
+    constexpr int XW = L::XW, XC = L::XC;
+    static_assert((WS * 4) % 16 == 0 && (XW * 4) % 16 == 0 && (XC * 4) % 16 == 0 && (TX * 4) % 16 == 0 &&
+                      WS <= 256 && RY <= 256,
+                  "TMA box");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* rU = reinterpret_cast<float*>(smem_raw);             // [NR][RY][WS]
-    float* rP = rU + NR * PL;                                    // [NR][RY][WS]
-    uint32_t* rG = reinterpret_cast<uint32_t*>(rP + NR * PL);   // [NR][RY][WS]
-    float* rX = reinterpret_cast<float*>(rG + NR * PL);         // [NR][TY][TX]
-    float* ePK = rX + NR * NI;                                   // [2][RY][WS]
+    __shared__ __align__(8) uint64_t mbar[NR];
+    // ring planes start on 128-byte boundaries (TMA destinations)
+    const uint32_t raw_base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    unsigned char* smem = smem_raw + ((128u - (raw_base & 127u)) & 127u);
+    float* rU = reinterpret_cast<float*>(smem);                  // [NR][RY][WS] (stride PLA)
+    float* rP = rU + NR * PLA;                                   // [NR][RY][WS]
+    uint32_t* rG = reinterpret_cast<uint32_t*>(rP + NR * PLA);  // [NR][RY][WS]
+    float* rX = reinterpret_cast<float*>(rG + NR * PLA);        // [NR][TY][TX] (stride NIA)
+    float* ePK = rX + NR * NIA;                                  // [2][RY][WS]
     float* eWY = ePK + 2 * PL;                                   // [2][RY][WS]
     float* eWX4 = eWY + 2 * PL;                                  // [2][RY][WS]
     float* eUN = eWX4 + 2 * PL;                                  // [2][RY][WS]
@@ -164,7 +207,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
     const bool has_down = ry + 1 < RY;
     const int wofs = ry * WS + V * sx;         // this strip in a plane
     const int sofs = ry * SX + sx;             // this strip in a strip array
-    const int xofs = y * TX + V * (sx - 1);    // this strip in the delta ring (inner only)
+    const int xofs = y * XW + V * sx - XC;     // this strip in the delta ring (inner only)
 
     const int tpb = A.ntx * A.nty * A.nzc;
     const int64_t nwork = (int64_t)(A.list ? *A.nlist : A.bx.nbox) * tpb;
@@ -172,7 +215,17 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
     const int64_t plane = (int64_t)PX * PY;
     const int64_t bstride = plane * A.pz;
     const float c2 = A.c2f, wmin = A.wminf;
-    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t sU = (uint32_t)__cvta_generic_to_shared(rU), sP = (uint32_t)__cvta_generic_to_shared(rP);
+    const uint32_t sG = (uint32_t)__cvta_generic_to_shared(rG), sX = (uint32_t)__cvta_generic_to_shared(rX);
+    const uint32_t sB = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) mbar_init(sB + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t seq = 0;      // planes issued by this CTA so far (the same in every thread)
+    bool waited_out = false;
 
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
         const int li = (int)(w / tpb);  // position in the list of active systems
@@ -193,33 +246,42 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
         if (z0 < ez) {
             // padded coordinates of this strip: x + V, y + 2, z + 2
             const int64_t base = (int64_t)box * bstride + (int64_t)(ty * TY + ry + 1) * PX + tx * TX + V * sx;
-            const float* Ub = static_cast<const float*>(A.u_in) + base;
-            const float* Pb = static_cast<const float*>(A.p_in) + base;
-            const uint32_t* Gb = A.gc + base;
             float* Xb = static_cast<float*>(A.x) + base;
             float* Uo = static_cast<float*>(A.u_out) + base;
             float* Po = static_cast<float*>(A.p_out) + base;
 
-            auto slot = [](int z) { return (z + 2 * NR) % NR; };
+            // plane z of this work item is the CTA's load number q(z); it sits
+            // in ring slot q % NR and completes phase (q / NR) & 1 of its mbarrier
+            const uint32_t q0 = seq - (uint32_t)(z0 - 1);
+            auto slot = [&](int z) { return (int)((q0 + (uint32_t)z) % NR); };
+            auto phase = [&](int z) { return ((q0 + (uint32_t)z) / NR) & 1u; };
+            // TMA box origins: the tile's first strip and row (x = -V, y = -1)
+            // for u, p, g; row y = 0 from column x = XC - V for delta
+            const int cx = tx * TX, cy = ty * TY + 1;
+            const int cz = box * A.pz + 2;
             auto issue = [&](int z) {
-                if (!live) return;
-                const int64_t pz = (int64_t)(z + 2) * plane;
-                const uint32_t so = (uint32_t)((slot(z) * PL + wofs) * 4);
-                cp_async_v<V>(s_base + so, Ub + pz);
-                cp_async_v<V>(s_base + (uint32_t)(NR * PL * 4) + so, Pb + pz);
-                cp_async_v<V>(s_base + (uint32_t)(2 * NR * PL * 4) + so, Gb + pz);
-                if (inner && z >= z0 && z < z1)
-                    cp_async_v<V>(s_base + (uint32_t)((3 * NR * PL + slot(z) * NI + xofs) * 4), Xb + pz);
+                if (tid != 0) return;
+                const int sl = slot(z);
+                const uint32_t bar = sB + 8 * sl;
+                const bool wx = z >= z0 && z < z1;
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_expect_tx(bar, (uint32_t)(3 * PL * 4 + (wx ? XW * TY * 4 : 0)));
+                tma_load3(sU + sl * PLA * 4, &A.tm.u, cx, cy, cz + z, bar);
+                tma_load3(sP + sl * PLA * 4, &A.tm.p, cx, cy, cz + z, bar);
+                tma_load3(sG + sl * PLA * 4, &A.tm.g, cx, cy, cz + z, bar);
+                if (wx) tma_load3(sX + sl * NIA * 4, &A.tm.x, cx + XC, cy + 1, cz + z, bar);
             };
 
             // One plane step.  At entry `in` holds the strip's registers for
             // plane z; `out` receives those for plane z+1.  BC = z & 1.
             auto step = [&](const int z, const StripState<V>& in, StripState<V>& out, auto bcc) {
                 constexpr int BC = decltype(bcc)::value, BN = BC ^ 1;
-                cp_async_wait<D - 1>();
+                if (!waited_out && !mbar_wait(sB + 8 * slot(z + 1), phase(z + 1))) {
+                    waited_out = true;
+                    if (A.err) atomicExch(A.err, 1);
+                }
                 __syncthreads();
                 if (z + 1 + D <= z1 + 1) issue(z + 1 + D);
-                cp_async_commit();
                 const int sn = slot(z + 1);
 
                 // -- 1: plane z+1 enters: p_k and the z edge (z, z+1)
@@ -229,9 +291,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 for (int i = 0; i < V; ++i) pkn[i] = wz0[i] = 0.0f, gn[i] = GC_ABSENT;
                 if (live) {
                     float uu[V], pp[V];
-                    ldv<V>(rU + sn * PL + wofs, uu);
-                    ldv<V>(rP + sn * PL + wofs, pp);
-                    ldv<V>(rG + sn * PL + wofs, gn);
+                    ldv<V>(rU + sn * PLA + wofs, uu);
+                    ldv<V>(rP + sn * PLA + wofs, pp);
+                    ldv<V>(rG + sn * PLA + wofs, gn);
 #pragma unroll
                     for (int i = 0; i < V; ++i) pkn[i] = fmaf(bp, pp[i], ku * uu[i]);
                     if (sten) {
@@ -249,7 +311,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 for (int i = 0; i < V; ++i) un0[i] = 0.0f;
                 if (sten && z >= z0) {
                     float uu[V], puu[V], pdd[V], wuu[V], wy0[V], wx0[V];
-                    ldv<V>(rU + slot(z) * PL + wofs, uu);
+                    ldv<V>(rU + slot(z) * PLA + wofs, uu);
                     const float pl = ePL[BC * PS + sofs - 1];
                     const float pr = has_right ? ePF[BC * PS + sofs + 1] : 0.0f;
                     const float wl = eWX[BC * PS + sofs - 1];
@@ -278,7 +340,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                     if (inner && z < z1) {
                         const int64_t pz = (int64_t)(z + 2) * plane;
                         float xn[V];
-                        ldv<V>(rX + slot(z) * NI + xofs, xn);
+                        ldv<V>(rX + slot(z) * NIA + xofs, xn);
 #pragma unroll
                         for (int i = 0; i < V; ++i) xn[i] = fmaf(alpha, in.pk0[i], xn[i]);
                         stv<V>(Uo + pz, un0);
@@ -321,10 +383,10 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 // the halo, strip 0 needs its last x weight and row -1 its y
                 // weights; row TY+1 none.
                 if (live && ry < RY - 1) {
-                    const uint32_t gr = has_right ? rG[sn * PL + wofs + V] : GC_ABSENT;
+                    const uint32_t gr = has_right ? rG[sn * PLA + wofs + V] : GC_ABSENT;
                     uint32_t gdd[V];
                     if (has_down) {
-                        ldv<V>(rG + sn * PL + wofs + WS, gdd);
+                        ldv<V>(rG + sn * PLA + wofs + WS, gdd);
                     } else {
 #pragma unroll
                         for (int i = 0; i < V; ++i) gdd[i] = GC_ABSENT;
@@ -349,10 +411,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
             };
 
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
+            for (int d = 0; d < D; ++d)
                 if (z0 - 1 + d <= z1 + 1) issue(z0 - 1 + d);
-                cp_async_commit();
-            }
             StripState<V> sa, sb;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
@@ -365,7 +425,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const SweepArgs A) {
                 step(z + 1, sb, sa, std::integral_constant<int, 1>());
             }
             if (z <= z1) step(z, sa, sb, std::integral_constant<int, 0>());
-            cp_async_wait<0>();
+            seq += (uint32_t)(z1 - z0 + 3);  // planes z0-1 .. z1+1
         }
         const float fv[6] = {a_gam, a_rr, a_del, a_eps, a_pi, a_tau};
         double v[6];
