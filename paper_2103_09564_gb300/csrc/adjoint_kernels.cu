@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjArgs a) {
     const int64_t li = (int64_t)blockIdx.x * 256 + threadIdx.x;
     double db = 0.0;
     if (li < nvox) {
-        const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+        int x, y, z;
+        vox_xyz(li, nx, ny, nvox, &x, &y, &z);
         int ex = nx, ey = ny, ez = nz;
         if (a.bx.ext) {
             ex = a.bx.ext[3 * box];

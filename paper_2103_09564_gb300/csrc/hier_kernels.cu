@@ -152,7 +152,8 @@ __global__ void k_gather(const GatherArgs a) {
     const int64_t nvox = (int64_t)nx * ny * nz;
     const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= nvox) return;
-    const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+    int x, y, z;
+    vox_xyz(li, nx, ny, nvox, &x, &y, &z);
     const BrickJob J = a.jobs[box];
     const int64_t i = (int64_t)box * nvox + li;
     if (x >= J.ex || y >= J.ey || z >= J.ez) {
@@ -276,7 +277,8 @@ __global__ void k_fill(const FillArgs a) {
     const int64_t n = (int64_t)a.lx * a.ly * a.lz;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int X = (int)(i % a.lx), Y = (int)((i / a.lx) % a.ly), Z = (int)(i / ((int64_t)a.lx * a.ly));
+    int X, Y, Z;
+    vox_xyz(i, a.lx, a.ly, n, &X, &Y, &Z);
     const int64_t b = ((int64_t)(Z / a.s) * a.nby + (Y / a.s)) * a.nbx + (X / a.s);
     const uint8_t st = a.status[b];
     if (st == 1) return;

@@ -108,6 +108,21 @@ __host__ __device__ __forceinline__ int64_t vec_index(const Pad& pd, const Boxes
     return (((int64_t)box * pd.pz + (z + 2)) * pd.py + (y + 2)) * pd.px + (x + pd.mx);
 }
 
+// (x, y, z) of the linear index li of an nx * ny * nz box: 32-bit division
+// when the box has fewer than 2^31 voxels, 64-bit otherwise.
+__host__ __device__ __forceinline__ void vox_xyz(int64_t li, int nx, int ny, int64_t nvox, int* x, int* y, int* z) {
+    if (nvox <= 0x7fffffff) {
+        const uint32_t l = (uint32_t)li, q = l / (uint32_t)nx;
+        *x = (int)(l - q * (uint32_t)nx);
+        *y = (int)(q % (uint32_t)ny);
+        *z = (int)(q / (uint32_t)ny);
+    } else {
+        *x = (int)(li % nx);
+        *y = (int)((li / nx) % ny);
+        *z = (int)(li / ((int64_t)nx * ny));
+    }
+}
+
 // Residual / initial guess (solve_kernels.cu).
 struct ResidArgs {
     Boxes bx;

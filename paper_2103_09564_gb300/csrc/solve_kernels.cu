@@ -134,7 +134,8 @@ __global__ void k_init_x(const ResidArgs a) {
     if (li >= nvox) return;
     int ex, ey, ez;
     box_extent(a.bx, box, &ex, &ey, &ez);
-    const int x = (int)(li % a.bx.nx), y = (int)((li / a.bx.nx) % a.bx.ny), z = (int)(li / ((int64_t)a.bx.nx * a.bx.ny));
+    int x, y, z;
+    vox_xyz(li, a.bx.nx, a.bx.ny, nvox, &x, &y, &z);
     const int64_t i = (int64_t)box * nvox + li;
     double v = 0.0;
     if (x < ex && y < ey && z < ez) {
@@ -155,11 +156,13 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
     const int nx = a.bx.nx, ny = a.bx.ny, nz = a.bx.nz;
     const int64_t nvox = (int64_t)nx * ny * nz;
     const int64_t li = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    double bb = 0, rr = 0, ns = 0, nf = 0;
+    double bb = 0, rr = 0;
+    int ns = 0, nf = 0;
     if (li < nvox) {
         int ex, ey, ez;
         box_extent(a.bx, box, &ex, &ey, &ez);
-        const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+        int x, y, z;
+        vox_xyz(li, nx, ny, nvox, &x, &y, &z);
         // (u, p, delta follow a.pad; x_hi, g and the code the caller layout)
         const int64_t base = (int64_t)box * nvox;
         const int64_t i = base + li;
@@ -199,7 +202,10 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                 const double r = rh - s;
                 bb = b * b;
                 rr = r * r;
-                uo = d > 0.0 ? (T)(r / d) : (T)0;
+                // u is stored in T: for FP32 the quotient of the rounded
+                // operands is as accurate as the stored value
+                if constexpr (sizeof(T) == 4) uo = d > 0.0 ? (float)r / (float)d : 0.0f;
+                else uo = d > 0.0 ? (T)(r / d) : (T)0;
             }
         }
         const int64_t v = vec_index(a.pad, a.bx, box, x, y, z);
@@ -213,9 +219,9 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
     for (int o = 16; o > 0; o >>= 1) {
         bb += __shfl_down_sync(0xffffffffu, bb, o);
         rr += __shfl_down_sync(0xffffffffu, rr, o);
-        ns += __shfl_down_sync(0xffffffffu, ns, o);
-        nf += __shfl_down_sync(0xffffffffu, nf, o);
     }
+    ns = __reduce_add_sync(0xffffffffu, ns);
+    nf = __reduce_add_sync(0xffffffffu, nf);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][wid] = bb;
@@ -241,7 +247,8 @@ __global__ void k_weights64(const ResidArgs a, double* w3) {
     if (li >= nvox) return;
     int ex, ey, ez;
     box_extent(a.bx, box, &ex, &ey, &ez);
-    const int x = (int)(li % nx), y = (int)((li / nx) % ny), z = (int)(li / ((int64_t)nx * ny));
+    int x, y, z;
+    vox_xyz(li, nx, ny, nvox, &x, &y, &z);
     const int64_t i = (int64_t)box * nvox + li;
     double wv[3] = {0.0, 0.0, 0.0};
     if (x < ex && y < ey && z < ez && a.code[i] != ABSENT) {
@@ -418,7 +425,8 @@ __global__ void k_accumulate(const Boxes bx, const Pad pad, const uint8_t* code,
     if (li >= nvox) return;
     const int64_t i = (int64_t)box * nvox + li;
     if (code[i] != FREE) return;
-    const int xx = (int)(li % bx.nx), yy = (int)((li / bx.nx) % bx.ny), zz = (int)(li / ((int64_t)bx.nx * bx.ny));
+    int xx, yy, zz;
+    vox_xyz(li, bx.nx, bx.ny, nvox, &xx, &yy, &zz);
     x[i] += (double)delta[vec_index(pad, bx, box, xx, yy, zz)];
 }
 
@@ -443,7 +451,8 @@ __global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtyp
     if (li >= nvox) return;
     int ex, ey, ez;
     box_extent(bx, box, &ex, &ey, &ez);
-    const int x = (int)(li % bx.nx), y = (int)((li / bx.nx) % bx.ny), z = (int)(li / ((int64_t)bx.nx * bx.ny));
+    int x, y, z;
+    vox_xyz(li, bx.nx, bx.ny, nvox, &x, &y, &z);
     const int64_t i = (int64_t)box * nvox + li;
     uint32_t w = fmt ? GC_ABSENT : 0u;
     if (x < ex && y < ey && z < ez) {
