@@ -36,10 +36,10 @@ TOL = 1e-8
 # (1 B).  The sweep kernel itself moves 28 B (g and code packed in one word).
 SWEEP_BYTES_PER_VOXEL = 27
 KERNEL_BYTES_PER_VOXEL = 28
-# DRAM bytes of one sweep launch on the 256^3 workload, from an ncu capture of
-# this benchmark (median over the timed step's sweeps); reset to None when the
-# sweep kernel changes until it is captured again
-SWEEP_TRAFFIC_256 = None
+# DRAM bytes of one sweep launch on the 256^3 workload per tile, from an ncu
+# launch list of this benchmark (median over the timed step's sweeps); cleared
+# when the sweep kernel changes until it is captured again
+SWEEP_TRAFFIC_256 = {"s32x22": 466.88e6}
 def _workload(n):
     return f"plain random walker, {n}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
 
@@ -242,6 +242,7 @@ def run(args):
             pg.destroy_process_group()
         return 0
     peak, src = _peaks()
+    tile_name = {v: k for k, v in rw._abi.RW_TILE.items()}.get(stats[0]["tile"], str(stats[0]["tile"]))
     # sweeps that did work: the PCG iterations plus the restart / replacement
     # sweep that opens each refinement round (launches after convergence exit
     # at once; their time stays in ms_sweeps, which makes this conservative)
@@ -256,13 +257,14 @@ def run(args):
                        "precision": "FP32 vectors/stencil, FP64 reductions + FP64-residual refinement",
                        "tol": TOL, "iters_per_solve": stats[0]["iters"], "refine_rounds": stats[0]["refine_rounds"],
                        "rel_resid": stats[0]["rel_resid"], "replicas": ws,
-                       "tile": {v: k for k, v in rw._abi.RW_TILE.items()}.get(stats[0]["tile"], stats[0]["tile"]),
+                       "tile": tile_name,
                        "sweeps_per_graph": stats[0]["iters_per_graph"],
                        "l2": "inputs larger than L2 (about 470 MB streamed per sweep), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_256 if N == 256 else None,
+                         "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_256.get(tile_name) if N == 256 else None,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, median over "
-                                           "the timed step's k_sweep5 launches (profiles/k_sweep5_plain256.md)",
+                                           "the timed step's k_sweep5 launches of this tile "
+                                           "(profiles/launches_plain256.md)",
                          "kernel": "k_sweep5 (fused PCG sweep)", "peak_source": src,
                          "algorithmic_bytes_per_launch": alg, "basis": "27 B per free voxel per sweep",
                          "kernel_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL, "launch_ms": t_launch_s * 1e3,
