@@ -17,7 +17,11 @@ namespace {
     X(27, 64, 11, 2, 480, 2, 2)   \
     X(28, 32, 12, 2, 288, 2, 3)   \
     X(29, 40, 20, 2, 512, 2, 2)   \
-    X(30, 40, 8, 2, 256, 2, 4)
+    X(30, 40, 8, 2, 256, 2, 4)    \
+    X(31, 32, 20, 4, 256, 3, 2)   \
+    X(32, 64, 8, 4, 224, 3, 2)    \
+    X(33, 32, 22, 4, 256, 1, 2)   \
+    X(34, 64, 8, 4, 224, 1, 3)
 
 template <int TX, int TY, int V, int NT, int D, int MB>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
