@@ -296,7 +296,7 @@ def run_hier(args):
     dev = torch.device("cuda", 0)
     ph = P.vessel_tree(n=n, seed=0, device=dev)
     xyz, val = _labels_np(ph)
-    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=args.leaf_host)
     del ph
     opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol)
     tree = rw.Tree(pyr, opts)
@@ -328,7 +328,8 @@ def run_hier(args):
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"hierarchical random walker, {n}^3 uint16 vessel tree (phantoms.vessel_tree, "
-                                   f"seed 0, 200 segments), brick {s}, e 1.25, pruning hom+dt, tol {args.tol}",
+                                   f"seed 0, 200 segments), brick {s}, e 1.25, pruning hom+dt, tol {args.tol}"
+                                   + (", leaf level in host memory" if args.leaf_host else ""),
                        "levels": per_level, "bricks_solved_per_run": stats[0]["bricks_solved"],
                        "bricks_pruned_per_run": stats[0]["bricks_pruned"], "labels": int(len(val))},
             "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s",
@@ -427,6 +428,8 @@ def main():
                          "adjoint: 32 x 96^3 differentiable batch")
     ap.add_argument("--brick", type=int, default=32)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--leaf-host", action="store_true",
+                    help="hier: leaf level in mapped host memory (out-of-core placement)")
     ap.add_argument("--n", type=int, default=0,
                     help="volume edge (default: 256 plain, 1024 hier, 96 adjoint; smaller for profiling)")
     args = ap.parse_args()

@@ -218,6 +218,18 @@ rw_status rw_solve_adjoint(const rw_volume* vol, const rw_seed_mask* seeds, cons
  * level is the 2x2x2 mean (existing children only at odd borders, Sec. IV-A)
  * with ceil-halved dims, until every dim is <= brick_size (the root). */
 rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid** out, void* stream);
+
+/* rw_build_pyramid with placement flags.  RW_PYR_LEAF_HOST: the leaf level
+ * (its unorm16 intensities here, and the leaf probability fields of every
+ * tree created on this pyramid) lives in pinned, mapped host memory instead
+ * of HBM; the GPU reads and writes it in place over the host link.  This is
+ * the out-of-core mode of Sec. III (volumes whose leaf does not fit in GPU
+ * memory): only the coarser levels (about 1/7 of the leaf) and the brick
+ * batches of one level occupy HBM.  Results are identical to the HBM
+ * placement.  Unknown flag bits: RW_ERR_INVALID_ARG. */
+#define RW_PYR_LEAF_HOST 1
+rw_status rw_build_pyramid_ex(const rw_volume* vol, int32_t brick_size, int32_t flags, rw_pyramid** out,
+                              void* stream);
 /* Number of levels and their dims (levels x 3, x/y/z; level 0 = root). */
 rw_status rw_pyramid_info(const rw_pyramid* pyr, int32_t* n_levels, int64_t* dims);
 /* Copy level `level` (FP32 intensities; the leaf as q / 65535) to `out`. */

@@ -242,10 +242,17 @@ class Pyramid:
             pass
 
 
-def rw_build_pyramid(volume, brick_size=32, *, lo=0.0, hi=1.0, normalize=False) -> Pyramid:
+RW_PYR_LEAF_HOST = 1
+
+
+def rw_build_pyramid(volume, brick_size=32, *, lo=0.0, hi=1.0, normalize=False, leaf_in_host=False) -> Pyramid:
+    """leaf_in_host: keep the leaf level (and the leaf fields of trees built on
+    this pyramid) in mapped host memory, read and written by the GPU in place
+    (out-of-core placement for volumes whose leaf does not fit in HBM)."""
     v, va, _ = _volume(volume, lo, hi, normalize, RW_STORE_UNORM16, False)
     h = ctypes.c_void_p(0)
-    _check(load().rw_build_pyramid(ctypes.byref(v), brick_size, ctypes.byref(h), _stream(va)))
+    flags = RW_PYR_LEAF_HOST if leaf_in_host else 0
+    _check(load().rw_build_pyramid_ex(ctypes.byref(v), brick_size, flags, ctypes.byref(h), _stream(va)))
     return Pyramid(h.value)
 
 

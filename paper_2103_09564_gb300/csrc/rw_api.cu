@@ -1003,18 +1003,47 @@ struct rw_pyramid {
     int K = 0;                               // leaf level index
     int s = 32;
     std::vector<std::array<int, 3>> dims;    // level 0 (root) .. K (leaf), x/y/z
-    uint16_t* leaf = nullptr;                // unorm16 leaf
+    uint16_t* leaf = nullptr;                // unorm16 leaf (device address)
     std::vector<float*> lv;                  // FP32 levels 0..K-1 (lv[K] = nullptr)
     int device = 0;
+    int leaf_host = 0;                       // leaf level in mapped host memory
+    void* leaf_host_ptr = nullptr;           // its host allocation
 };
+
+namespace {
+
+// Level storage: HBM, or pinned host memory mapped into the device's address
+// space (the out-of-core placement of the leaf level).
+cudaError_t level_alloc(bool host, size_t bytes, void** dev, void** host_ptr) {
+    *dev = nullptr;
+    *host_ptr = nullptr;
+    if (!host) return cudaMalloc(dev, bytes);
+    cudaError_t e = cudaHostAlloc(host_ptr, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return e;
+    e = cudaHostGetDevicePointer(dev, *host_ptr, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(*host_ptr);
+        *host_ptr = nullptr;
+    }
+    return e;
+}
+
+void level_free(void* dev, void* host_ptr) {
+    if (host_ptr) cudaFreeHost(host_ptr);
+    else if (dev) cudaFree(dev);
+}
+
+}  // namespace
 
 namespace {
 
 struct TreeLevel {
     int nbx = 1, nby = 1, nbz = 1;
     int64_t nb = 1;
-    float* P = nullptr;      // filled field
+    float* P = nullptr;      // filled field (device address)
     float* Pold = nullptr;   // previous filled field (incremental pass)
+    void* P_host = nullptr;  // host allocations when the level lives in host memory
+    void* Pold_host = nullptr;
     std::vector<int32_t> flags;
     std::vector<float> mn, mx, md;
     std::vector<uint8_t> status;  // 0 absent, 1 solved (new values), 2 reused (old values)
@@ -1340,8 +1369,14 @@ rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
 extern "C" {
 
 rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid** out, void* stream) {
+    return rw_build_pyramid_ex(vol, brick_size, 0, out, stream);
+}
+
+rw_status rw_build_pyramid_ex(const rw_volume* vol, int32_t brick_size, int32_t flags, rw_pyramid** out,
+                              void* stream) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     if (!out) return fail(RW_ERR_INVALID_ARG, "out is NULL");
+    if (flags & ~RW_PYR_LEAF_HOST) return fail(RW_ERR_INVALID_ARG, "unknown pyramid flags 0x%x", flags);
     *out = nullptr;
     int64_t nvox = 0, batch = 1;
     RCK(check_volume(vol, &nvox, &batch));
@@ -1366,7 +1401,10 @@ rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid*
         rw_pyramid_free(py);
         return st;
     };
-    cudaError_t e = cudaMalloc(&py->leaf, nvox * 2);
+    py->leaf_host = (flags & RW_PYR_LEAF_HOST) ? 1 : 0;
+    void* leaf_dev = nullptr;
+    cudaError_t e = level_alloc(py->leaf_host, nvox * 2, &leaf_dev, &py->leaf_host_ptr);
+    py->leaf = static_cast<uint16_t*>(leaf_dev);
     if (e != cudaSuccess) return cleanup(fail(RW_ERR_OOM, "pyramid leaf: %s", cudaGetErrorString(e)));
     for (int k = 0; k < py->K; ++k) {
         const int64_t n = (int64_t)dims[k][0] * dims[k][1] * dims[k][2];
@@ -1417,7 +1455,7 @@ rw_status rw_pyramid_read_level(const rw_pyramid* py, int32_t level, float* out,
 
 void rw_pyramid_free(rw_pyramid* py) {
     if (!py) return;
-    if (py->leaf) cudaFree(py->leaf);
+    level_free(py->leaf, py->leaf_host_ptr);
     for (float* p : py->lv)
         if (p) cudaFree(p);
     delete py;
@@ -1444,10 +1482,15 @@ rw_status rw_tree_create(const rw_pyramid* py, const rw_opts* opts_in, rw_tree**
         L.nbz = (d[2] + py->s - 1) / py->s;
         L.nb = (int64_t)L.nbx * L.nby * L.nbz;
         const int64_t n = (int64_t)d[0] * d[1] * d[2];
-        cudaError_t e = cudaMalloc(&L.P, n * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&L.Pold, n * 4);
+        const bool host = py->leaf_host && k == py->K;
+        void *p0 = nullptr, *p1 = nullptr;
+        cudaError_t e = level_alloc(host, n * 4, &p0, &L.P_host);
+        L.P = static_cast<float*>(p0);
+        if (e == cudaSuccess) e = level_alloc(host, n * 4, &p1, &L.Pold_host);
+        L.Pold = static_cast<float*>(p1);
         if (e == cudaSuccess) e = cudaMemset(L.P, 0, n * 4);
         if (e == cudaSuccess) e = cudaMemset(L.Pold, 0, n * 4);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             rw_tree_free(t);
             return fail(RW_ERR_OOM, "tree level %d: %s", k, cudaGetErrorString(e));
@@ -1505,7 +1548,10 @@ rw_status rw_update_seeds(rw_tree* t, const rw_labels* added, rw_stats* stats, v
     RCK(copy_labels(t, added, 1));
     DevWorkspace* w = nullptr;
     RCK(enter(&w, stream));
-    for (auto& L : t->L) std::swap(L.P, L.Pold);
+    for (auto& L : t->L) {
+        std::swap(L.P, L.Pold);
+        std::swap(L.P_host, L.Pold_host);
+    }
     t->update = 1;
     t->resolve.clear();
     t->reused.clear();
@@ -1561,8 +1607,8 @@ rw_status rw_tree_node_stats(const rw_tree* t, int32_t level, int64_t* n_nodes, 
 void rw_tree_free(rw_tree* t) {
     if (!t) return;
     for (auto& L : t->L) {
-        if (L.P) cudaFree(L.P);
-        if (L.Pold) cudaFree(L.Pold);
+        level_free(L.P, L.P_host);
+        level_free(L.Pold, L.Pold_host);
     }
     delete t;
 }
