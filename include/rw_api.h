@@ -89,11 +89,18 @@ typedef struct rw_seed_mask {
 
 /* Label points (Sec. IV-A: labels are 3-D points with a value in [0, 1]).
  * HOST memory.  xyz: n x 3 leaf-voxel coordinates (x, y, z); voxel i spans
- * [i, i + 1).  At level k a label falls into voxel floor(q / 2^(K-k)). */
+ * [i, i + 1).  At level k a label falls into voxel floor(q / 2^(K-k)); a
+ * voxel holding labels of different values is a conflict (unseeded).
+ * cls (nullable): the class of each label in a multi-class labelling (one
+ * tree per class, class c's labels with value 1, the others 0).  With it, a
+ * voxel holding labels of different classes is a conflict as well, so that
+ * every class tree leaves the same voxels unseeded and the class
+ * probabilities sum to one (Sec. III-B). */
 typedef struct rw_labels {
     const double* xyz;
     const float* value;
     int64_t n;
+    const int32_t* cls;
 } rw_labels;
 
 typedef struct rw_opts {
@@ -256,6 +263,19 @@ rw_status rw_refine_level(rw_tree* tree, int32_t level, const rw_labels* labels,
  * labels) nor prunable are re-solved from the old field; similar nodes keep
  * their old values and whole old subtree.  Requires a fully refined tree. */
 rw_status rw_update_seeds(rw_tree* tree, const rw_labels* added, rw_stats* stats, void* stream);
+
+/* Multi-class labelling (Sec. III-B: one random-walker problem per class,
+ * class c's labels as 1 and every other class's as 0; the label of a voxel is
+ * the class of highest probability).  `trees` holds one refined tree per
+ * class (2 <= n_classes <= RW_MAX_CLASSES), all on one pyramid.  Over box
+ * [x0,x1) x [y0,y1) x [z0,z1) of `level` (box NULL: the whole level) writes
+ * labels_out[i] = argmax_c P_c[i] (ties: the lowest class index) and, when
+ * prob_out is not NULL, the winning probability.  Outputs: host or device
+ * memory, x fastest.  RW_ERR_INVALID_ARG for a bad count, level or box, or
+ * trees on different pyramids. */
+#define RW_MAX_CLASSES 8
+rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_t level, const int64_t box[6],
+                          uint8_t* labels_out, float* prob_out, void* stream);
 
 /* Copy box [x0,x1) x [y0,y1) x [z0,z1) (box = {x0,y0,z0,x1,y1,z1}) of the
  * filled probability field of `level` to `out` (x fastest). */

@@ -77,6 +77,7 @@ class Tree:
     labels_value: np.ndarray
     opts: Opts
     stats: dict = field(default_factory=dict)
+    labels_cls: np.ndarray | None = None   # class of each label (multi-class), or None
 
 
 def margins(s: int, e: float):
@@ -111,9 +112,12 @@ def upsample(prev: np.ndarray, shape) -> np.ndarray:
     return out
 
 
-def rasterize(xyz: np.ndarray, val: np.ndarray, K: int, k: int, shape, added=None):
-    """T_k of Sec. IV-A: map label points to level-k voxels.
-    Returns (seeds: {(z,y,x): value}, conflicts: {(z,y,x): involves_added})."""
+def rasterize(xyz: np.ndarray, val: np.ndarray, K: int, k: int, shape, added=None, cls=None):
+    """T_k of Sec. IV-A: map label points to level-k voxels.  A voxel holding
+    labels of different values (or, with `cls`, of different classes: the
+    multi-class reading, the same unseeded voxels in every class problem) is
+    a conflict.  Returns (seeds: {(z,y,x): value}, conflicts: {(z,y,x):
+    involves_added})."""
     scale = 2.0 ** (-(K - k))
     groups = {}
     for n in range(len(val)):
@@ -121,14 +125,16 @@ def rasterize(xyz: np.ndarray, val: np.ndarray, K: int, k: int, shape, added=Non
         x, y, z = int(v[0]), int(v[1]), int(v[2])
         if not (0 <= x < shape[2] and 0 <= y < shape[1] and 0 <= z < shape[0]):
             continue
-        groups.setdefault((z, y, x), []).append((float(val[n]), bool(added[n]) if added is not None else False))
+        groups.setdefault((z, y, x), []).append((float(val[n]), bool(added[n]) if added is not None else False,
+                                                 int(cls[n]) if cls is not None else -1))
     seeds, conflicts = {}, {}
     for key, items in groups.items():
-        vals = {a for a, _ in items}
-        if len(vals) == 1:
+        vals = {a for a, _, _ in items}
+        classes = {c for _, _, c in items if c >= 0}
+        if len(vals) == 1 and len(classes) <= 1:
             seeds[key] = items[0][0]
         else:
-            conflicts[key] = any(f for _, f in items)
+            conflicts[key] = any(f for _, f, _ in items)
     return seeds, conflicts
 
 
@@ -207,7 +213,7 @@ def _children(b, shape_next, s):
     return out
 
 
-def run(levels, labels_xyz, labels_value, opts: Opts | None = None) -> Tree:
+def run(levels, labels_xyz, labels_value, opts: Opts | None = None, labels_cls=None) -> Tree:
     """Full top-down run of H_p (Eqs. 1-3 with pruning).  Returns the tree with
     the filled probability field of every level; P[-1] is the result."""
     opts = opts or Opts()
@@ -219,7 +225,7 @@ def run(levels, labels_xyz, labels_value, opts: Opts | None = None) -> Tree:
     for k in range(K + 1):
         shape = levels[k].shape
         Up = upsample(P[k - 1], shape) if k > 0 else None
-        seeds, conflicts = rasterize(labels_xyz, labels_value, K, k, shape)
+        seeds, conflicts = rasterize(labels_xyz, labels_value, K, k, shape, cls=labels_cls)
         Pk = Up.copy() if Up is not None else np.zeros(shape, dtype=np.float64)
         init = Pk.copy()
         lvl = {}
@@ -241,10 +247,11 @@ def run(levels, labels_xyz, labels_value, opts: Opts | None = None) -> Tree:
         info.append(lvl)
         active = sorted(set(nxt))
     return Tree(levels=levels, P=P, info=info, labels_xyz=np.asarray(labels_xyz, dtype=np.float64).reshape(-1, 3),
-                labels_value=np.asarray(labels_value, dtype=np.float64), opts=opts, stats=st)
+                labels_value=np.asarray(labels_value, dtype=np.float64), opts=opts, stats=st,
+                labels_cls=None if labels_cls is None else np.asarray(labels_cls, dtype=np.int64).reshape(-1))
 
 
-def update(old: Tree, add_xyz, add_value) -> Tree:
+def update(old: Tree, add_xyz, add_value, add_cls=None) -> Tree:
     """Incremental labelling (Sec. IV-E).  The root is re-solved (initialised
     with the old root); at every level the children of re-solved nodes that are
     neither similar nor prunable are re-solved (initialised with the old filled
@@ -258,6 +265,11 @@ def update(old: Tree, add_xyz, add_value) -> Tree:
     xyz = np.concatenate([old.labels_xyz, add_xyz])
     val = np.concatenate([old.labels_value, add_value])
     added = np.concatenate([np.zeros(len(old.labels_value), bool), np.ones(len(add_value), bool)])
+    cls = None
+    if old.labels_cls is not None or add_cls is not None:
+        oc = old.labels_cls if old.labels_cls is not None else np.full(len(old.labels_value), -1)
+        ac = np.asarray(add_cls).reshape(-1) if add_cls is not None else np.full(len(add_value), -1)
+        cls = np.concatenate([oc, ac]).astype(np.int64)
     P, info = [], []
     resolve = [(0, 0, 0)]
     reused = []
@@ -265,7 +277,7 @@ def update(old: Tree, add_xyz, add_value) -> Tree:
     for k in range(K + 1):
         shape = levels[k].shape
         Up = upsample(P[k - 1], shape) if k > 0 else None
-        seeds, conflicts = rasterize(xyz, val, K, k, shape, added)
+        seeds, conflicts = rasterize(xyz, val, K, k, shape, added, cls)
         Pk = Up.copy() if Up is not None else np.zeros(shape, dtype=np.float64)
         Pold = old.P[k]
         for b in reused:
@@ -306,4 +318,5 @@ def update(old: Tree, add_xyz, add_value) -> Tree:
         info.append(lvl)
         resolve = sorted(set(nxt_resolve))
         reused = sorted(set(nxt_reused))
-    return Tree(levels=levels, P=P, info=info, labels_xyz=xyz, labels_value=val, opts=opts, stats=st)
+    return Tree(levels=levels, P=P, info=info, labels_xyz=xyz, labels_value=val, opts=opts, stats=st,
+                labels_cls=cls)

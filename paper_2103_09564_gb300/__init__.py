@@ -22,7 +22,8 @@ from ._abi import (RW_CODE_ABSENT, RW_CODE_FREE, RW_CODE_SEED, RW_FP64, RW_MIXED
                    RW_NODE_CFL_ADDED, RW_NODE_DT, RW_NODE_HOM, RW_NODE_NO_SEEDS, RW_NODE_PRUNABLE, RW_NODE_REUSED,
                    RW_NODE_SIMILAR, RW_NODE_SOLVED, RW_STORE_F32, RW_STORE_UNORM16, LibraryMissing)
 
-__all__ = ["RWError", "Opts", "rw_solve", "rw_solve_noalloc", "rw_solve_adjoint", "rw_build_pyramid", "Pyramid", "Tree", "load",
+__all__ = ["RWError", "Opts", "rw_solve", "rw_solve_noalloc", "rw_solve_adjoint", "rw_build_pyramid", "Pyramid", "Tree",
+           "trees_argmax", "load",
            "release_workspace", "version"]
 
 
@@ -256,11 +257,38 @@ def rw_build_pyramid(volume, brick_size=32, *, lo=0.0, hi=1.0, normalize=False, 
     return Pyramid(h.value)
 
 
-def _labels(xyz, value):
+RW_MAX_CLASSES = 8
+
+
+def trees_argmax(trees, level=None, box=None, out=None, prob=None):
+    """Multi-class labels: argmax over one refined tree per class (ties: the
+    lowest class index) on `level` (default: the leaf).  Returns (labels
+    uint8, winning probability float32 or None); host (numpy) arrays unless
+    CUDA tensors are passed as `out` / `prob`."""
+    if not 2 <= len(trees) <= RW_MAX_CLASSES:
+        raise ValueError(f"need 2..{RW_MAX_CLASSES} trees")
+    pyr = trees[0].pyr
+    if level is None:
+        level = pyr.levels - 1
+    x, y, z = pyr.dims[level]
+    b = np.array(box if box is not None else [0, 0, 0, x, y, z], dtype=np.int64)
+    shape = (int(b[5] - b[2]), int(b[4] - b[1]), int(b[3] - b[0]))
+    if out is None:
+        out = np.empty(shape, dtype=np.uint8)
+    o = _Arr(out)
+    p = _Arr(prob) if prob is not None else None
+    arr = (ctypes.c_void_p * len(trees))(*[t.h.value for t in trees])
+    _check(load().rw_trees_argmax(arr, len(trees), level, b.ctypes.data, o.ptr, p.ptr if p else None,
+                                  _stream(o, *( [p] if p else []))))
+    return o.obj, (p.obj if p else None)
+
+
+def _labels(xyz, value, cls=None):
     xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
     val = np.ascontiguousarray(np.asarray(value, dtype=np.float32).reshape(-1))
-    lab = _abi.rw_labels(xyz.ctypes.data, val.ctypes.data, len(val))
-    return lab, (xyz, val)
+    c = None if cls is None else np.ascontiguousarray(np.asarray(cls, dtype=np.int32).reshape(-1))
+    lab = _abi.rw_labels(xyz.ctypes.data, val.ctypes.data, len(val), c.ctypes.data if c is not None else None)
+    return lab, (xyz, val, c)
 
 
 class Tree:
@@ -273,20 +301,21 @@ class Tree:
         _check(load().rw_tree_create(pyramid.h, ctypes.byref(self.opts), ctypes.byref(h)))
         self.h = h
 
-    def refine_level(self, level, xyz=None, value=None):
+    def refine_level(self, level, xyz=None, value=None, cls=None):
         st = _abi.rw_stats()
         if xyz is not None:
-            lab, keep = _labels(xyz, value)
+            lab, keep = _labels(xyz, value, cls)
             _check(load().rw_refine_level(self.h, level, ctypes.byref(lab), ctypes.byref(st), None))
         else:
             _check(load().rw_refine_level(self.h, level, None, ctypes.byref(st), None))
         return st.as_dict()
 
-    def run(self, xyz, value):
-        """All levels, root to leaf; returns the summed stats."""
+    def run(self, xyz, value, cls=None):
+        """All levels, root to leaf; returns the summed stats.  cls: the class
+        of each label in a multi-class labelling (class-aware conflicts)."""
         tot = {}
         for k in range(self.pyr.levels):
-            s = self.refine_level(k, xyz if k == 0 else None, value if k == 0 else None)
+            s = self.refine_level(k, xyz if k == 0 else None, value if k == 0 else None, cls if k == 0 else None)
             for key, v in s.items():
                 if key in ("iters", "refine_rounds"):
                     tot[key] = max(tot.get(key, 0), v)
@@ -296,8 +325,8 @@ class Tree:
                     tot[key] = tot.get(key, 0) + v
         return tot
 
-    def update_seeds(self, xyz, value):
-        lab, keep = _labels(xyz, value)
+    def update_seeds(self, xyz, value, cls=None):
+        lab, keep = _labels(xyz, value, cls)
         st = _abi.rw_stats()
         _check(load().rw_update_seeds(self.h, ctypes.byref(lab), ctypes.byref(st), None))
         return st.as_dict()

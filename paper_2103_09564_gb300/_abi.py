@@ -29,7 +29,8 @@ RW_TILE = {"auto": 0, "32x16": 1, "64x8": 2, "40x8": 3, "40x20": 4, "80x8": 5, "
 EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspace", "rw_solve", "rw_solve_noalloc",
            "rw_solve_adjoint",
            "rw_build_pyramid", "rw_build_pyramid_ex", "rw_pyramid_info", "rw_pyramid_read_level", "rw_pyramid_free", "rw_tree_create",
-           "rw_refine_level", "rw_update_seeds", "rw_tree_read_level", "rw_tree_node_stats", "rw_tree_free"]
+           "rw_refine_level", "rw_update_seeds", "rw_tree_read_level", "rw_tree_node_stats", "rw_tree_free",
+           "rw_trees_argmax"]
 
 
 class rw_volume(ctypes.Structure):
@@ -43,7 +44,7 @@ class rw_seed_mask(ctypes.Structure):
 
 
 class rw_labels(ctypes.Structure):
-    _fields_ = [("xyz", ctypes.c_void_p), ("value", ctypes.c_void_p), ("n", ctypes.c_int64)]
+    _fields_ = [("xyz", ctypes.c_void_p), ("value", ctypes.c_void_p), ("n", ctypes.c_int64), ("cls", ctypes.c_void_p)]
 
 
 class rw_opts(ctypes.Structure):
@@ -81,6 +82,7 @@ PROTOTYPES = {
     "rw_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(rw_volume), ctypes.POINTER(rw_seed_mask),
                                         ctypes.POINTER(rw_opts), _P, _P, _P, _P, ctypes.POINTER(rw_stats), _P]),
     "rw_build_pyramid": (ctypes.c_int, [ctypes.POINTER(rw_volume), ctypes.c_int32, ctypes.POINTER(_P), _P]),
+    "rw_trees_argmax": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
     "rw_build_pyramid_ex": (ctypes.c_int, [ctypes.POINTER(rw_volume), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P),
                                            _P]),
     "rw_pyramid_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P]),

@@ -304,6 +304,39 @@ __global__ void k_read_box(const float* field, int lx, int ly, int x0, int y0, i
     out[k] = field[((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x)];
 }
 
+// Multi-class labels: argmax over the class fields of one level (ties: the
+// lowest class index) on a box of the level.
+__global__ void k_argmax(const ClassFields f, int lx, int ly, int x0, int y0, int z0, int bx, int by, int bz,
+                         uint8_t* labels, float* prob) {
+    const int64_t n = (int64_t)bx * by * bz;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int x, y, z;
+    vox_xyz(k, bx, by, n, &x, &y, &z);
+    const int64_t i = ((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x);
+    int best = 0;
+    float pb = f.P[0][i];
+    for (int c = 1; c < f.n; ++c) {
+        const float v = f.P[c][i];
+        if (v > pb) {
+            pb = v;
+            best = c;
+        }
+    }
+    labels[k] = (uint8_t)best;
+    if (prob) prob[k] = pb;
+}
+
+cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t box[6], uint8_t* labels, float* prob,
+                          cudaStream_t s) {
+    const int bx = (int)(box[3] - box[0]), by = (int)(box[4] - box[1]), bz = (int)(box[5] - box[2]);
+    const int64_t n = (int64_t)bx * by * bz;
+    if (n == 0) return cudaSuccess;
+    k_argmax<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, lx, ly, (int)box[0], (int)box[1], (int)box[2], bx, by, bz,
+                                                          labels, prob);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_read_box(const float* field, int lx, int ly, int lz, const int64_t box[6], float* out,
                             cudaStream_t s) {
     (void)lz;

@@ -1058,6 +1058,7 @@ struct rw_tree {
     std::vector<double> lab_xyz;
     std::vector<float> lab_val;
     std::vector<uint8_t> lab_added;
+    std::vector<int32_t> lab_cls;  // class of each label, -1 when not given
     int refined = 0;         // levels of the current pass done
     int update = 0;          // current pass is incremental
     std::vector<std::array<int, 3>> resolve, reused;  // node lists for the next level
@@ -1069,6 +1070,7 @@ struct LabelKey {
     float value;
     int conflict;
     int added;
+    int32_t cls;
 };
 
 void rasterize(const rw_tree* t, int k, std::vector<LabelVox>* out) {
@@ -1085,11 +1087,14 @@ void rasterize(const rw_tree* t, int k, std::vector<LabelVox>* out) {
         if (!(fx >= 0 && fy >= 0 && fz >= 0 && fx < d[0] && fy < d[1] && fz < d[2])) continue;
         const int64_t key = ((int64_t)fz * d[1] + (int64_t)fy) * d[0] + (int64_t)fx;
         auto it = m.find(key);
+        const int32_t c = t->lab_cls[i];
         if (it == m.end()) {
-            m[key] = LabelKey{t->lab_val[i], 0, t->lab_added[i] ? 1 : 0};
+            m[key] = LabelKey{t->lab_val[i], 0, t->lab_added[i] ? 1 : 0, c};
             order.push_back(key);
         } else {
             if (it->second.value != t->lab_val[i]) it->second.conflict = 1;
+            if (c >= 0 && it->second.cls >= 0 && c != it->second.cls) it->second.conflict = 1;
+            if (it->second.cls < 0) it->second.cls = c;
             if (t->lab_added[i]) it->second.added = 1;
         }
     }
@@ -1352,7 +1357,7 @@ rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
 rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
     if (!lab || lab->n <= 0) return RW_OK;
     if (!lab->xyz || !lab->value) return fail(RW_ERR_INVALID_ARG, "labels with NULL arrays");
-    if (is_device_ptr(lab->xyz) || is_device_ptr(lab->value))
+    if (is_device_ptr(lab->xyz) || is_device_ptr(lab->value) || (lab->cls && is_device_ptr(lab->cls)))
         return fail(RW_ERR_INVALID_ARG, "labels must be in host memory");
     for (int64_t i = 0; i < lab->n; ++i) {
         t->lab_xyz.push_back(lab->xyz[3 * i]);
@@ -1360,6 +1365,7 @@ rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
         t->lab_xyz.push_back(lab->xyz[3 * i + 2]);
         t->lab_val.push_back(lab->value[i]);
         t->lab_added.push_back((uint8_t)added);
+        t->lab_cls.push_back(lab->cls ? lab->cls[i] : -1);
     }
     return RW_OK;
 }
@@ -1518,6 +1524,7 @@ rw_status rw_refine_level(rw_tree* t, int32_t level, const rw_labels* labels, rw
             t->lab_xyz.clear();
             t->lab_val.clear();
             t->lab_added.clear();
+            t->lab_cls.clear();
             RCK(copy_labels(t, labels, 0));
         }
         t->update = 0;
@@ -1588,6 +1595,42 @@ rw_status rw_tree_read_level(const rw_tree* t, int32_t level, const int64_t box[
     if (!dev) RCK(ws_get_t(w, S_OUT, n * 4, &dst));
     CK(counted(launch_read_box(t->L[level].P, d[0], d[1], d[2], bb, dst, w->stream)));
     if (!dev) CK(cudaMemcpyAsync(out, dst, n * 4, cudaMemcpyDeviceToHost, w->stream));
+    return leave(w);
+}
+
+rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_t level, const int64_t box[6],
+                          uint8_t* labels_out, float* prob_out, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    static_assert(RW_MAX_CLASSES == 8, "ClassFields holds 8 fields");
+    if (!trees || !labels_out || n_classes < 2 || n_classes > RW_MAX_CLASSES)
+        return fail(RW_ERR_INVALID_ARG, "need 2..%d trees and an output", RW_MAX_CLASSES);
+    ClassFields cf{};
+    cf.n = n_classes;
+    const rw_pyramid* py = nullptr;
+    for (int c = 0; c < n_classes; ++c) {
+        if (!trees[c]) return fail(RW_ERR_INVALID_ARG, "tree %d is NULL", c);
+        if (c == 0) py = trees[c]->pyr;
+        else if (trees[c]->pyr != py) return fail(RW_ERR_INVALID_ARG, "trees on different pyramids");
+    }
+    if (level < 0 || level > py->K) return fail(RW_ERR_INVALID_ARG, "level %d out of range", level);
+    for (int c = 0; c < n_classes; ++c) cf.P[c] = trees[c]->L[level].P;
+    const auto& d = py->dims[level];
+    int64_t bb[6] = {0, 0, 0, d[0], d[1], d[2]};
+    if (box)
+        for (int i = 0; i < 6; ++i) bb[i] = box[i];
+    for (int a = 0; a < 3; ++a)
+        if (bb[a] < 0 || bb[a + 3] > d[a] || bb[a] > bb[a + 3]) return fail(RW_ERR_INVALID_ARG, "box outside level");
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    const int64_t n = (bb[3] - bb[0]) * (bb[4] - bb[1]) * (bb[5] - bb[2]);
+    uint8_t* lab = labels_out;
+    float* prob = prob_out;
+    const bool lab_dev = is_device_ptr(labels_out), prob_dev = !prob_out || is_device_ptr(prob_out);
+    if (!lab_dev) RCK(ws_get_t(w, S_CODE, n, &lab));
+    if (!prob_dev) RCK(ws_get_t(w, S_OUT, n * 4, &prob));
+    CK(counted(launch_argmax(cf, d[0], d[1], bb, lab, prob, w->stream)));
+    if (!lab_dev) CK(cudaMemcpyAsync(labels_out, lab, n, cudaMemcpyDeviceToHost, w->stream));
+    if (!prob_dev) CK(cudaMemcpyAsync(prob_out, prob, n * 4, cudaMemcpyDeviceToHost, w->stream));
     return leave(w);
 }
 

@@ -248,6 +248,13 @@ struct FillArgs {
     int nbx, nby, nbz, s;
 };
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s);
+// Class fields of one level for the multi-class argmax.
+struct ClassFields {
+    const float* P[8];
+    int n;
+};
+cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t box[6], uint8_t* labels, float* prob,
+                          cudaStream_t s);
 cudaError_t launch_read_box(const float* field, int lx, int ly, int lz, const int64_t box[6], float* out,
                             cudaStream_t s);
 

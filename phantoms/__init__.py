@@ -324,23 +324,9 @@ def _seg_dist2(px, py, pz, a, b):
     return dx * dx + dy * dy + dz * dz
 
 
-def vessel_tree(n=1024, seed=0, n_segments=200, r_max=12.0, r_min=2.0, shape=None,
-                fg=(3000.0, 400.0), bg=(800.0, 300.0), salt=0.01, salt_value=5000, device=None):
-    """Branching vessel tree phantom (uint16) with labels.
-
-    Breadth-first bifurcation from a root at a random border point: each segment
-    has length 5 x radius, splits into two children of radius r/sqrt(2) (area
-    preserving, clamped to r_min) at random angles of 15-60 degrees, with a
-    sphere at every joint.  Intensities: vessel N(3000, 400), background
-    N(800, 300), then a fraction ``salt`` of voxels set to ``salt_value``.
-    Labels: two centre-line points per segment (value 1) and two points two
-    radii away, outside every vessel (value 0).  Radii and lengths scale with
-    n/1024 so that smaller volumes keep the same structure.
-    Returns ``volume`` (uint16), ``labels_xyz`` (float64, (N, 3)),
-    ``labels_value`` (float32), ``mask`` (bool), ``lo``/``hi`` window (0, 5000).
-    """
-    if shape is None:
-        shape = (n, n, n)
+def _vessel_geometry(shape, seed, n_segments, r_max, r_min):
+    """Segments, rasterised mask and the geometry stream (it continues into
+    the label placement) of the branching vessel tree."""
     nz, ny, nx = shape
     dims = np.array([nx, ny, nz], dtype=np.float64)
     sc = min(dims) / 1024.0
@@ -390,6 +376,30 @@ def vessel_tree(n=1024, seed=0, n_segments=200, r_max=12.0, r_min=2.0, shape=Non
         dist2 = np.minimum(_seg_dist2(px, py, pz, a, b),
                            (px - b[0]) ** 2 + (py - b[1]) ** 2 + (pz - b[2]) ** 2)
         mask[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] |= dist2 <= r * r
+
+    return segs, mask, st
+
+
+def vessel_tree(n=1024, seed=0, n_segments=200, r_max=12.0, r_min=2.0, shape=None,
+                fg=(3000.0, 400.0), bg=(800.0, 300.0), salt=0.01, salt_value=5000, device=None):
+    """Branching vessel tree phantom (uint16) with labels.
+
+    Breadth-first bifurcation from a root at a random border point: each segment
+    has length 5 x radius, splits into two children of radius r/sqrt(2) (area
+    preserving, clamped to r_min) at random angles of 15-60 degrees, with a
+    sphere at every joint.  Intensities: vessel N(3000, 400), background
+    N(800, 300), then a fraction ``salt`` of voxels set to ``salt_value``.
+    Labels: two centre-line points per segment (value 1) and two points two
+    radii away, outside every vessel (value 0).  Radii and lengths scale with
+    n/1024 so that smaller volumes keep the same structure.
+    Returns ``volume`` (uint16), ``labels_xyz`` (float64, (N, 3)),
+    ``labels_value`` (float32), ``mask`` (bool), ``lo``/``hi`` window (0, 5000).
+    """
+    if shape is None:
+        shape = (n, n, n)
+    nz, ny, nx = shape
+    dims = np.array([nx, ny, nz], dtype=np.float64)
+    segs, mask, st = _vessel_geometry(shape, seed, n_segments, r_max, r_min)
 
     plane = nx * ny
     if device is not None:
@@ -450,6 +460,91 @@ def vessel_tree(n=1024, seed=0, n_segments=200, r_max=12.0, r_min=2.0, shape=Non
     return {"volume": vol, "labels_xyz": np.array(lx, dtype=np.float64).reshape(-1, 3),
             "labels_value": np.array(lv, dtype=np.float32), "mask": mask,
             "lo": 0.0, "hi": 5000.0, "beta": 130.0, "segments": segs}
+
+
+def multiclass_case(shape=(128, 128, 128), seed=0, n_segments=40, n_blobs=60, strokes_per_class=3,
+                    stroke_len=200, n_updates=10, device=None):
+    """Three-class phantom for multi-class labelling (shape z, y, x).
+
+    Classes: 0 background, 1 branching vessel tree (as in vessel_tree, radii
+    scaled with the smallest dim), 2 cell blobs (random rotated ellipsoids,
+    semi-axes U(4, 15) scaled, vessels take precedence).  Intensities per
+    class N(800, 250), N(3000, 250), N(2000, 250) (sigma = 5 % of the window
+    [0, 5000]), rounded to uint16.  Strokes: `strokes_per_class` polylines of
+    `stroke_len` voxels inside each class, then `n_updates` further strokes
+    in random classes (for incremental updates).  Each stroke is (xyz voxel
+    centres (L, 3) float64, class).  Returns ``volume`` (uint16, a torch
+    tensor on `device` when given), ``classes`` (uint8), ``strokes``,
+    ``updates``, ``lo``/``hi``."""
+    nz, ny, nx = shape
+    segs, vmask, _ = _vessel_geometry(shape, seed, n_segments, 12.0, 2.0)
+    classes = np.zeros(shape, dtype=np.uint8)
+    st = Stream(seed, 31)
+    sc = min(shape) / 1024.0
+    for _ in range(n_blobs):
+        c = np.array([st.uniform(0, nx), st.uniform(0, ny), st.uniform(0, nz)])
+        ax = np.array([st.uniform(4.0, 15.0) for _ in range(3)]) * max(sc * 4.0, 0.5)
+        R = st.rotation()
+        r = float(ax.max())
+        lo = np.maximum(np.floor(c - r - 1).astype(int), 0)
+        hi = np.minimum(np.ceil(c + r + 1).astype(int), [nx, ny, nz])
+        if np.any(hi <= lo):
+            continue
+        px = np.arange(lo[0], hi[0], dtype=np.float64)[None, None, :] + 0.5 - c[0]
+        py = np.arange(lo[1], hi[1], dtype=np.float64)[None, :, None] + 0.5 - c[1]
+        pz = np.arange(lo[2], hi[2], dtype=np.float64)[:, None, None] + 0.5 - c[2]
+        q = [R[0, k] * px + R[1, k] * py + R[2, k] * pz for k in range(3)]
+        inside = (q[0] / ax[0]) ** 2 + (q[1] / ax[1]) ** 2 + (q[2] / ax[2]) ** 2 <= 1.0
+        sub = classes[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        sub[inside] = 2
+    classes[vmask] = 1
+    means = np.array([800.0, 3000.0, 2000.0])
+    plane = nx * ny
+    if device is not None:
+        import torch
+        cl_t = torch.from_numpy(classes).to(device)
+        mean_t = torch.tensor(means, device=device)
+        vol_t = torch.empty(shape, dtype=torch.int32, device=device)
+        zslab = max(1, (1 << 25) // plane)
+        for z0 in range(0, nz, zslab):
+            z1 = min(nz, z0 + zslab)
+            idx = torch.arange(z0 * plane, z1 * plane, dtype=torch.int64, device=device)
+            v = mean_t[cl_t[z0:z1].reshape(-1).long()] + 250.0 * normal_torch(seed, 3, idx)
+            vol_t[z0:z1] = v.round().clamp(0, 65535).to(torch.int32).reshape(z1 - z0, ny, nx)
+        vol = vol_t.to(torch.uint16) if hasattr(torch, "uint16") else vol_t
+    else:
+        vol = np.empty(shape, dtype=np.uint16)
+        zslab = max(1, (1 << 22) // plane)
+        for z0 in range(0, nz, zslab):
+            z1 = min(nz, z0 + zslab)
+            idx = np.arange(z0 * plane, z1 * plane, dtype=np.uint64)
+            v = means[classes[z0:z1].reshape(-1)] + 250.0 * normal(seed, 3, idx)
+            vol[z0:z1] = np.clip(np.rint(v), 0, 65535).astype(np.uint16).reshape(z1 - z0, ny, nx)
+    ss = Stream(seed, 41)
+
+    def stroke(c):
+        inside = lambda p: classes[int(p[2]), int(p[1]), int(p[0])] == c
+        pts = _polyline(ss, inside, shape, length=stroke_len)
+        return np.array([(x + 0.5, y + 0.5, z + 0.5) for (x, y, z) in pts], dtype=np.float64).reshape(-1, 3)
+
+    strokes = [(stroke(c), c) for c in range(3) for _ in range(strokes_per_class)]
+    updates = []
+    for _ in range(n_updates):
+        c = int(ss.uniform(0, 3)) % 3
+        updates.append((stroke(c), c))
+    return {"volume": vol, "classes": classes, "strokes": strokes, "updates": updates, "lo": 0.0, "hi": 5000.0,
+            "beta": 130.0}
+
+
+def class_labels(strokes, c):
+    """Labels of the class-c problem: (xyz, value, class) with class-c stroke
+    points 1 and the others 0."""
+    if not strokes:
+        return np.zeros((0, 3)), np.zeros(0, dtype=np.float32), np.zeros(0, dtype=np.int32)
+    xyz = np.concatenate([s for s, _ in strokes], axis=0)
+    val = np.concatenate([np.full(len(s), 1.0 if k == c else 0.0, dtype=np.float32) for s, k in strokes])
+    cls = np.concatenate([np.full(len(s), k, dtype=np.int32) for s, k in strokes])
+    return xyz, val, cls
 
 
 def adjoint_batch(n: int = 96, batch: int = 32, seed0: int = 0):

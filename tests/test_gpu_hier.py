@@ -203,3 +203,60 @@ def test_leaf_in_host_memory_matches_hbm(rw):
         pyr.free()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+def _class_trees(rw, c, s, tol, prune):
+    pyr = rw.rw_build_pyramid(c["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    trees = []
+    for k in range(3):
+        t = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=tol, prune_hom=int(prune), prune_dt=0))
+        t.run(*P.class_labels(c["strokes"], k))
+        trees.append(t)
+    return pyr, trees
+
+
+def test_multiclass_argmax_matches_oracle(rw):
+    # one tree per class (Sec. III-B), no pruning: the GPU class fields sum to
+    # one and the fused argmax agrees with the oracle's per-class hierarchy on
+    # every voxel where the two best classes are more than 1e-3 apart
+    c = P.multiclass_case((64, 64, 64), seed=1, n_segments=20, n_blobs=30, n_updates=0)
+    pyr, trees = _class_trees(rw, c, 8, 1e-11, prune=False)
+    labels, pmax = rw.trees_argmax(trees, prob=np.empty((64, 64, 64), np.float32))
+    fields = np.stack([t.read_level(pyr.levels - 1) for t in trees])
+    assert np.array_equal(labels, np.argmax(fields, axis=0).astype(np.uint8))
+    assert np.array_equal(pmax, fields.max(axis=0))
+    q = O.quantize(c["volume"], 0.0, 5000.0, True)
+    seeds = np.zeros(q.shape, bool)
+    for xyz, _ in c["strokes"]:
+        v = np.floor(xyz).astype(int)
+        seeds[v[:, 2], v[:, 1], v[:, 0]] = True
+    det = determined_mask(O.leaf_level(q), 130.0, seeds=seeds)
+    assert det.mean() > 0.99
+    assert np.max(np.abs(fields.sum(axis=0) - 1.0)[det]) <= 1e-4
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=130.0, prune_hom=False, prune_dt=False)
+    of = []
+    for k in range(3):
+        xyz, val, cls = P.class_labels(c["strokes"], k)
+        of.append(hrw.run(levels, xyz, val, oo, labels_cls=cls).P[-1])
+    of = np.stack(of)
+    top2 = np.sort(of, axis=0)
+    clear = det & (top2[-1] - top2[-2] > 1e-3)
+    assert clear.mean() > 0.9
+    assert np.array_equal(labels[clear], np.argmax(of, axis=0)[clear])
+
+
+def test_argmax_ties_take_the_lowest_class(rw):
+    c = P.multiclass_case((32, 32, 32), seed=4, n_segments=8, n_blobs=10, n_updates=0)
+    pyr = rw.rw_build_pyramid(c["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    lab = P.class_labels(c["strokes"], 1)
+    trees = []
+    for _ in range(2):
+        t = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-10, tile="32x8"))
+        t.run(*lab)
+        trees.append(t)
+    labels, _ = rw.trees_argmax(trees)
+    assert np.array_equal(trees[0].read_level(pyr.levels - 1), trees[1].read_level(pyr.levels - 1))
+    assert not labels.any()
+    with pytest.raises(rw.RWError):
+        rw.trees_argmax(trees, box=[0, 0, 0, 999, 1, 1])

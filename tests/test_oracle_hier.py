@@ -161,3 +161,29 @@ def test_upsample_pins():
     expect = (np.arange(16) + 0.5) / 2.0 - 0.5
     assert np.allclose(up[0, 0, 1:-1], expect[1:-1], atol=0, rtol=0)
     assert up[0, 0, 0] == 0.0 and up[0, 0, -1] == 7.0
+
+
+def test_multiclass_hierarchy_sums_to_one():
+    # One problem per class (class k's strokes as 1, the others as 0; a voxel
+    # with strokes of two classes unseeded in every problem): at the root the
+    # class probabilities sum to one (Sec. III-B); the border seeds of every
+    # finer neighbourhood are interpolated parent probabilities, so without
+    # pruning the sum stays one at every level (to solver tolerance).  The
+    # 64^3 case has strokes of different classes in one coarse voxel.
+    for shape, kw in (((24, 24, 24), dict(n_segments=6, n_blobs=8, strokes_per_class=2, stroke_len=30)),
+                      ((64, 64, 64), dict(n_segments=20, n_blobs=30))):
+        _sum_to_one(shape, kw)
+
+
+def _sum_to_one(shape, kw):
+    c = P.multiclass_case(shape, seed=2 if shape[0] == 24 else 1, n_updates=0, **kw)
+    q = O.quantize(c["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=130.0, prune_hom=False, prune_dt=False)
+    fields = []
+    for k in range(3):
+        xyz, val, cls = P.class_labels(c["strokes"], k)
+        fields.append(hrw.run(levels, xyz, val, oo, labels_cls=cls).P)
+    for lev in range(len(levels)):
+        total = fields[0][lev] + fields[1][lev] + fields[2][lev]
+        assert np.max(np.abs(total - 1.0)) <= 1e-9, lev
