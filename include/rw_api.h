@@ -121,7 +121,18 @@ typedef struct rw_opts {
     int32_t tile;          /* sweep tile: 0 = autotuned choice, else an RW_TILE_* value */
     int32_t batch_bricks;  /* 1: one batched launch per level (default); 0: bricks one by one */
     int32_t max_batch;     /* bricks per batched launch, default 8192 */
+    int32_t weight;        /* rw_weight: edge weight function, default RW_WEIGHT_GAUSSIAN */
 } rw_opts;
+
+/* Edge weight functions (Sec. III-B / III-C).
+ *   RW_WEIGHT_GAUSSIAN: w = max(exp(-beta (g_p - g_q)^2), w_min).
+ *   RW_WEIGHT_POISSON:  the weight for Poisson noise of the paper's case
+ *     study, w = exp(-(sqrt(n_p) - sqrt(n_q))^2 / 2) on raw counts n; here
+ *     n = beta * g (beta = the count that g = 1 stands for, e.g. the window's
+ *     hi with lo = 0), i.e. w = max(exp(-(beta / 2) (sqrt(g_p) - sqrt(g_q))^2),
+ *     w_min).  Forward solves only (rw_solve, the hierarchy); rw_solve_adjoint
+ *     and rw_solve_noalloc return RW_ERR_UNIMPLEMENTED. */
+typedef enum { RW_WEIGHT_GAUSSIAN = 0, RW_WEIGHT_POISSON = 1 } rw_weight;
 
 enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, RW_TILE_40x20 = 4,
        RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7, RW_TILE_32x32 = 8, RW_TILE_64x16 = 9,

@@ -22,6 +22,7 @@ differences for the adjoint.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -123,17 +124,34 @@ def pyramid(leaf: np.ndarray, brick_size: int):
     return levels[::-1]
 
 
-def weight(a: float, b: float, beta: float, w_min: float = W_MIN) -> float:
+def weight(a: float, b: float, beta: float, w_min: float = W_MIN, kind: str = "gaussian") -> float:
+    """Edge weight between intensities a, b (Sec. III-B).  kind "poisson": the
+    case-study weight for Poisson noise, exp(-(sqrt(n_a) - sqrt(n_b))^2 / 2)
+    on counts n = beta * g, evaluated as the Gaussian form on sqrt(g) with
+    beta / 2 (the same expression), clamped at w_min."""
+    if kind == "poisson":
+        return float(lib().oracle_weight(math.sqrt(a), math.sqrt(b), beta / 2.0, w_min))
     return float(lib().oracle_weight(a, b, beta, w_min))
 
 
+def _weight_form(g, beta, kind):
+    """(intensities, beta) of the Gaussian form that gives weights `kind`."""
+    if kind == "poisson":
+        return np.sqrt(np.asarray(g, dtype=np.float64)), beta / 2.0
+    if kind != "gaussian":
+        raise ValueError(f"unknown weight kind {kind!r}")
+    return g, beta
+
+
 def rw_solve(g: np.ndarray, code: np.ndarray, xin: np.ndarray, beta: float, w_min: float = W_MIN,
-             tol: float = 1e-13, max_iter: int = 200000, rhs: np.ndarray | None = None):
+             tol: float = 1e-13, max_iter: int = 200000, rhs: np.ndarray | None = None, kind: str = "gaussian"):
     """Plain random walker (Sec. III-B) by FP64 Jacobi-PCG.
 
     g: intensities (FP64), code: 0 free / 1 seed / 2 absent, xin: seed values
     on seeds and the initial guess on free voxels.  Returns (x, iters, relres,
-    status) with status 0 ok, 2 no seeds, 3 not converged."""
+    status) with status 0 ok, 2 no seeds, 3 not converged.  kind: the weight
+    function ("gaussian", or "poisson" with beta the count scale)."""
+    g, beta = _weight_form(g, beta, kind)
     g = np.ascontiguousarray(g, dtype=np.float64)
     code = np.ascontiguousarray(code, dtype=np.uint8)
     xin = np.ascontiguousarray(xin, dtype=np.float64)
@@ -173,9 +191,9 @@ def adjoint_grad(g, code, x, lam, beta, w_min=W_MIN):
 
 
 def solve_volume(volume, code, value, beta, lo=0.0, hi=1.0, normalize=False, tol=1e-13,
-                 max_iter=200000, w_min=W_MIN, x0=None):
+                 max_iter=200000, w_min=W_MIN, x0=None, kind="gaussian"):
     """Quantise a raw volume, then solve it (the plain path end to end)."""
     q = quantize(volume, lo, hi, normalize)
     g = dequantize(q)
     xin = np.where(code == SEED, value.astype(np.float64), 0.0 if x0 is None else x0)
-    return rw_solve(g, code, xin, beta, w_min=w_min, tol=tol, max_iter=max_iter)
+    return rw_solve(g, code, xin, beta, w_min=w_min, tol=tol, max_iter=max_iter, kind=kind)

@@ -50,6 +50,7 @@ class Opts:
     prune_dt: bool = True
     tol: float = 1e-13
     max_iter: int = 200000
+    weight: str = "gaussian"    # edge weight function (oracle.rw_solve kind)
 
 
 @dataclass
@@ -185,7 +186,7 @@ def _solve_node(k, b, level, Up, init, seeds, conflicts, opts, shape):
         iters = 0
     else:
         x, iters, _, st = rw_solve(g, code, xin, opts.beta, w_min=opts.w_min, tol=opts.tol,
-                                   max_iter=opts.max_iter)
+                                   max_iter=opts.max_iter, kind=opts.weight)
     (bz0, bz1), (by0, by1), (bx0, bx1) = box
     out = x[bz0 - z0:bz1 - z0, by0 - y0:by1 - y0, bx0 - x0:bx1 - x0]
     nfree = int(np.count_nonzero(code == FREE))

@@ -53,7 +53,8 @@ def _check(st: int, allow=()):
 
 def Opts(**kw) -> _abi.rw_opts:
     """rw_opts with the library defaults, overridden by keyword (precision may
-    be 'mixed'/'fp64', tile a name such as '40x8')."""
+    be 'mixed'/'fp64', tile a name such as '40x8', weight 'gaussian'/'poisson'
+    -- for 'poisson', beta is the count that g = 1 stands for)."""
     o = _abi.rw_opts()
     load().rw_opts_default(ctypes.byref(o))
     for k, v in kw.items():
@@ -61,6 +62,8 @@ def Opts(**kw) -> _abi.rw_opts:
             v = {"mixed": RW_MIXED, "fp64": RW_FP64}[v]
         if k == "tile" and isinstance(v, str):
             v = _abi.RW_TILE[v]
+        if k == "weight" and isinstance(v, str):
+            v = {"gaussian": 0, "poisson": 1}[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(o, k, v)

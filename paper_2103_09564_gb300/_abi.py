@@ -53,7 +53,7 @@ class rw_opts(ctypes.Structure):
                 ("brick_size", ctypes.c_int32), ("expand", ctypes.c_float), ("t_hom", ctypes.c_float),
                 ("t_bin", ctypes.c_float), ("t_inc", ctypes.c_float), ("prune_hom", ctypes.c_int32),
                 ("prune_dt", ctypes.c_int32), ("iters_per_graph", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("batch_bricks", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+                ("batch_bricks", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("weight", ctypes.c_int32)]
 
 
 class rw_stats(ctypes.Structure):

@@ -165,7 +165,8 @@ rw_status leave(DevWorkspace* w) {
 rw_status check_opts(const rw_opts& o) {
     if (!(o.beta >= 0.0f) || !(o.w_min >= 0.0f) || !(o.tol >= 0.0) || o.max_iter < 1 || o.refine_rounds < 0 ||
         (o.precision != RW_MIXED && o.precision != RW_FP64) || o.iters_per_graph < 2 || o.tile < 0 || o.tile >= N_TILES ||
-        o.brick_size < 2 || !(o.expand >= 1.0f) || o.max_batch < 1)
+        o.brick_size < 2 || !(o.expand >= 1.0f) || o.max_batch < 1 ||
+        (o.weight != RW_WEIGHT_GAUSSIAN && o.weight != RW_WEIGHT_POISSON))
         return fail(RW_ERR_INVALID_ARG, "invalid rw_opts");
     return RW_OK;
 }
@@ -635,7 +636,11 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     ra.pad = ps.pad;
     ra.part = rpart;
     ra.blocks_per_box = bpb;
-    ra.mbeta = -(double)o.beta;
+    // Poisson weights: the Gaussian form on sqrt(g) with beta / 2
+    const bool poisson = o.weight == RW_WEIGHT_POISSON;
+    const double beta_w = poisson ? 0.5 * (double)o.beta : (double)o.beta;
+    ra.sqrt_g = poisson ? 1 : 0;
+    ra.mbeta = -beta_w;
     ra.wmin = (double)o.w_min;
 
     // FP64 edge weights once per solve (the residual rounds read them) while
@@ -656,7 +661,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
         const int fmt = ps.cands[0] >= TILE_STRIP_FIRST ? 1 : 0;
         if (fmt) CK(counted(launch_fill_u32(gc, ps.nvec, GC_ABSENT, w->stream)));
         else if (ps.pad.px) CK(cudaMemsetAsync(gc, 0, ps.nvec * 4, w->stream));
-        CK(counted(launch_pack_gc(bx, ps.pad, P.g, P.gtype, P.code, gc, w->stream, fmt)));
+        CK(counted(launch_pack_gc(bx, ps.pad, P.g, P.gtype, P.code, gc, w->stream, fmt, ra.sqrt_g)));
     }
     CK(cudaMemsetAsync(sc, 0, bx.nbox * sizeof(BoxScalars), w->stream));
     if (P.init_x) CK(counted(launch_init_x(cur64, ra, w->stream)));
@@ -675,9 +680,10 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     sa.n_active = nact;
     sa.err = nact + 1;  // the strip sweep's load-wait flag, next to the active count
     CK(cudaMemsetAsync(nact + 1, 0, sizeof(int), w->stream));
-    sa.c2f = (float)(-(double)o.beta * 1.4426950408889634);
+    sa.c2f = (float)(-beta_w * 1.4426950408889634);
+    sa.sqrt_g = ra.sqrt_g;
     sa.wminf = o.w_min;
-    sa.mbeta = -(double)o.beta;
+    sa.mbeta = -beta_w;
     sa.wmin = (double)o.w_min;
     sa.px = ps.pad.px;
     sa.py = ps.pad.py;
@@ -918,6 +924,7 @@ rw_status rw_solve_adjoint(const rw_volume* vol, const rw_seed_mask* seeds, cons
     if (opts_in) o = *opts_in;
     else rw_opts_default(&o);
     RCK(check_opts(o));
+    if (o.weight != RW_WEIGHT_GAUSSIAN) return fail(RW_ERR_UNIMPLEMENTED, "the adjoint supports Gaussian weights only");
     int64_t nvox = 0, batch = 1;
     RCK(check_volume(vol, &nvox, &batch));
     if (!seeds || !seeds->code || !x || !dloss_dx) return fail(RW_ERR_INVALID_ARG, "NULL argument");

@@ -69,6 +69,7 @@ struct SweepArgs {
     double mbeta;           // -beta, FP64 weights
     double wmin;
     int* err = nullptr;     // set to 1 by a strip sweep whose load wait ran out
+    int sqrt_g = 0;         // Poisson weights: FP64 sweep reads sqrt(g) (the g words are packed so)
     StripMaps tm;           // k_sweep5 only
 };
 
@@ -148,6 +149,7 @@ struct ResidArgs {
     // optional FP64 forward edge weights (+x, +y, +z planes of nbox*nvox
     // each, caller layout) from launch_weights64; null: computed in place
     const double* w3 = nullptr;
+    int sqrt_g = 0;  // Poisson weights: the Gaussian form on sqrt(g) (mbeta is then -beta/2)
 };
 cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s);
 // FP64 edge weights, each edge once (its lower voxel's forward edge), for the
@@ -171,7 +173,7 @@ cudaError_t launch_compact_active(const BoxScalars* sc, int nbox, int* list, int
 // (k_sweep5): +g free, -g seed, GC_ABSENT (a NaN) absent.
 constexpr uint32_t GC_ABSENT = 0xffc00000u;
 cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
-                           uint32_t* gc, cudaStream_t s, int fmt = 0);
+                           uint32_t* gc, cudaStream_t s, int fmt = 0, int sqrt_g = 0);
 cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s);
 
 // Normalisation / quantisation (hier_kernels.cu).

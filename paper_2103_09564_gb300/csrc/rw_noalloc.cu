@@ -105,6 +105,8 @@ extern "C" rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* 
     if (!vol || !vol->data || !seeds || !seeds->code || !x_out)
         return fail(RW_ERR_INVALID_ARG, "rw_solve_noalloc: NULL volume, seed code or output");
     if (o.precision != RW_MIXED) return fail(RW_ERR_INVALID_ARG, "rw_solve_noalloc: only RW_MIXED precision");
+    if (o.weight != RW_WEIGHT_GAUSSIAN)
+        return fail(RW_ERR_UNIMPLEMENTED, "rw_solve_noalloc: Gaussian weights only");
     if (!(o.tol >= 0.0) || o.max_iter < 1 || o.iters_per_graph < 2 || o.refine_rounds < 0)
         return fail(RW_ERR_INVALID_ARG, "rw_solve_noalloc: invalid rw_opts");
     if ((vol->dtype != RW_U16 && vol->dtype != RW_F32) || vol->storage != RW_STORE_UNORM16)

@@ -114,6 +114,12 @@ __device__ __forceinline__ double gdbl(const void* g, int gtype, int64_t i) {
                           : (double)static_cast<const float*>(g)[i];
 }
 
+// Intensity as the weights see it: g, or sqrt(g) for Poisson weights.
+__device__ __forceinline__ double gdbl_w(const ResidArgs& a, int64_t i) {
+    const double g = gdbl(a.g, a.gtype, i);
+    return a.sqrt_g ? sqrt(g) : g;
+}
+
 __device__ __forceinline__ bool box_extent(const Boxes& bx, int box, int* ex, int* ey, int* ez) {
     if (bx.ext) {
         *ex = bx.ext[3 * box];
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
             if (c == SEED) ns = 1;
             if (c == FREE) {
                 nf = 1;
-                const double gi = gdbl(a.g, a.gtype, i), xi = xh[i];
+                const double gi = gdbl_w(a, i), xi = xh[i];
                 const double rh = a.rhs ? (double)a.rhs[i] : 0.0;
                 double d = 0, s = 0, b = rh;
                 const int nbx[6] = {x - 1, x + 1, x, x, x, x};
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                         const int64_t ntot = (int64_t)a.bx.nbox * nvox;
                         w = a.w3[(int64_t)(k >> 1) * ntot + ((k & 1) ? i : j)];
                     } else {
-                        const double dg = gi - gdbl(a.g, a.gtype, j);
+                        const double dg = gi - gdbl_w(a, j);
                         w = fmax(exp(a.mbeta * dg * dg), a.wmin);
                     }
                     const double xj = xh[j];
@@ -253,7 +259,7 @@ __global__ void k_weights64(const ResidArgs a, double* w3) {
     const int64_t i = (int64_t)box * nvox + li;
     double wv[3] = {0.0, 0.0, 0.0};
     if (x < ex && y < ey && z < ez && a.code[i] != ABSENT) {
-        const double gi = gdbl(a.g, a.gtype, i);
+        const double gi = gdbl_w(a, i);
         const bool in[3] = {x + 1 < ex, y + 1 < ey, z + 1 < ez};
         const int64_t st[3] = {1, nx, (int64_t)nx * ny};
 #pragma unroll
@@ -261,7 +267,7 @@ __global__ void k_weights64(const ResidArgs a, double* w3) {
             if (!in[k]) continue;
             const int64_t j = i + st[k];
             if (a.code[j] == ABSENT) continue;
-            const double dg = gi - gdbl(a.g, a.gtype, j);
+            const double dg = gi - gdbl_w(a, j);
             wv[k] = fmax(exp(a.mbeta * dg * dg), a.wmin);
         }
     }
@@ -445,7 +451,7 @@ cudaError_t launch_accumulate(const Boxes& bx, const Pad& pad, const uint8_t* co
 // fmt 0: FP32 g with the code in its two lowest mantissa bits (0 absent,
 // 1 free, 2 seed); fmt 1: +g free, -g seed, NaN absent (g >= 0).
 __global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtype, const uint8_t* code,
-                          uint32_t* gc, int fmt) {
+                          uint32_t* gc, int fmt, int sqrt_g) {
     const int box = blockIdx.y;
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
     const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -458,8 +464,9 @@ __global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtyp
     uint32_t w = fmt ? GC_ABSENT : 0u;
     if (x < ex && y < ey && z < ez) {
         const uint8_t c = code[i];
-        const float gv = gtype == G_U16 ? (float)static_cast<const uint16_t*>(g)[i] * (1.0f / 65535.0f)
-                                        : static_cast<const float*>(g)[i];
+        float gv = gtype == G_U16 ? (float)static_cast<const uint16_t*>(g)[i] * (1.0f / 65535.0f)
+                                  : static_cast<const float*>(g)[i];
+        if (sqrt_g) gv = sqrtf(gv);
         if (fmt) {
             const uint32_t gb = __float_as_uint(fabsf(gv));
             w = c == FREE ? gb : (c == SEED ? (gb | 0x80000000u) : GC_ABSENT);
@@ -472,10 +479,10 @@ __global__ void k_pack_gc(const Boxes bx, const Pad pad, const void* g, int gtyp
 }
 
 cudaError_t launch_pack_gc(const Boxes& bx, const Pad& pad, const void* g, int gtype, const uint8_t* code,
-                           uint32_t* gc, cudaStream_t s, int fmt) {
+                           uint32_t* gc, cudaStream_t s, int fmt, int sqrt_g) {
     const int64_t nvox = (int64_t)bx.nx * bx.ny * bx.nz;
     dim3 grid((unsigned)((nvox + 255) / 256), (unsigned)bx.nbox);
-    k_pack_gc<<<grid, 256, 0, s>>>(bx, pad, g, gtype, code, gc, fmt);
+    k_pack_gc<<<grid, 256, 0, s>>>(bx, pad, g, gtype, code, gc, fmt, sqrt_g);
     return cudaGetLastError();
 }
 

@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs A) {
                         const int64_t i = base + ((int64_t)zf * ny + gy) * nx + gx;
                         c = cin[i];
                         gv = gval<T, G>(gin, i);
+                        if (A.sqrt_g) gv = sqrt(gv);
                         uk = Uin[i];
                         pm = Pin[i];
                     }

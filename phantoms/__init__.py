@@ -229,6 +229,29 @@ def pocket_case(n: int = 24, seed: int = 0, n_pairs: int = 6, bridge: float = 0.
     return {"volume": vol.astype(np.float32), "code": code, "value": value, "pairs": pairs, "beta": 130.0}
 
 
+def poisson_ball(n: int = 64, seed: int = 0, lam_fg: float = 100.0, lam_bg: float = 50.0):
+    """Photon-count ball for the Poisson weight function: counts with mean
+    lam_fg inside a ball of radius 0.3 n, lam_bg outside, drawn as
+    round(lam + sqrt(lam) N(0, 1)) clamped at 0 (the normal approximation of
+    Poisson noise), uint16.  Seeds as in ball_case (9-voxel foreground line,
+    border faces background)."""
+    shape = (n, n, n)
+    x, y, z = _centres(shape)
+    c = n / 2.0
+    r = 0.3 * n
+    mask = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2 <= r * r
+    lam = np.where(mask, lam_fg, lam_bg)
+    cnt = np.clip(np.rint(lam + np.sqrt(lam) * _voxel_noise(seed, 5, shape, 1.0)), 0, 65535).astype(np.uint16)
+    code = np.zeros(shape, dtype=np.uint8)
+    value = np.zeros(shape, dtype=np.float32)
+    code[border_faces(shape)] = 1
+    h = n // 2
+    a, b = max(h - 4, 1), min(h + 5, n - 1)
+    code[h, h, a:b] = 1
+    value[h, h, a:b] = 1.0
+    return {"volume": cnt, "code": code, "value": value, "mask": mask}
+
+
 def _polyline(st: Stream, inside, shape, length=40, max_tries=4000):
     nz, ny, nx = shape
     for _ in range(max_tries):

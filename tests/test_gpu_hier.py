@@ -64,7 +64,10 @@ def _compare(rw, tree, otree, opts, s, incremental=False):
                     excluded.append((k, b))
         field = tree.read_level(k).astype(np.float64)
         # trapped pockets (salt clusters behind w_min edges) are undetermined
-        mask = determined_mask(otree.levels[k], opts.beta)
+        if opts.weight == "poisson":
+            mask = determined_mask(np.sqrt(otree.levels[k]), opts.beta / 2.0)
+        else:
+            mask = determined_mask(otree.levels[k], opts.beta)
         for (kk, e) in excluded:
             sh = k - kk
             lo = [v * s * (1 << sh) for v in e]
@@ -260,3 +263,21 @@ def test_argmax_ties_take_the_lowest_class(rw):
     assert not labels.any()
     with pytest.raises(rw.RWError):
         rw.trees_argmax(trees, box=[0, 0, 0, 999, 1, 1])
+
+
+def test_poisson_weights_hierarchy_parity(rw):
+    S = 255.0
+    c = P.poisson_ball(n=64, seed=5)
+    h = 32
+    xyz = [(x + 0.5, h + 0.5, h + 0.5) for x in range(28, 37)]
+    xyz += [(a + 0.5, b + 0.5, d + 0.5) for a in (2, 61) for b in (2, 61) for d in (2, 61)]
+    val = np.array([1.0] * 9 + [0.0] * 8, np.float32)
+    xyz = np.array(xyz)
+    pyr = rw.rw_build_pyramid(c["volume"], 8, lo=0.0, hi=S, normalize=True)
+    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=S, tol=1e-11, weight="poisson"))
+    tree.run(xyz, val)
+    q = O.quantize(c["volume"], 0.0, S, True)
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=S, weight="poisson")
+    ot = hrw.run(levels, xyz, val, oo)
+    _compare(rw, tree, ot, oo, 8)

@@ -266,3 +266,26 @@ def test_weakly_attached_pairs_parity(rw, precision):
     assert np.max(np.abs(x - xo)) <= TOL
     for (z, y, xx) in c["pairs"]:
         assert abs(x[z, y, xx] - x[z, y + 1, xx]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_poisson_weights_parity(rw, precision):
+    # counts normalised by S = 255 (window [0, 255]); beta = S makes the
+    # weights exp(-(sqrt(n_p) - sqrt(n_q))^2 / 2) on the counts
+    S = 255.0
+    c = P.poisson_ball(n=48, seed=2)
+    x, st = rw.rw_solve(_cuda(c["volume"]), _cuda(c["code"]), _cuda(c["value"]),
+                        rw.Opts(beta=S, tol=1e-10, precision=precision, weight="poisson"),
+                        lo=0.0, hi=S, normalize=True)
+    xo, it, rr, so = O.solve_volume(c["volume"], c["code"], c["value"], S, lo=0.0, hi=S, normalize=True,
+                                    kind="poisson")
+    assert so == 0
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= TOL
+    with pytest.raises(rw.RWError):
+        rw.rw_solve_adjoint(_cuda(c["volume"].astype(np.float32) / S), _cuda(c["code"]), x,
+                            torch_ones_like(x), rw.Opts(beta=S, weight="poisson"))
+
+
+def torch_ones_like(x):
+    import torch
+    return torch.ones_like(x)

@@ -2,6 +2,8 @@
 do not come from the oracle: hand-derived closed forms, a dense direct solve of
 the defining linear system, the discrete maximum principle, multi-class
 sum-to-one, symmetry and special cases."""
+import math
+
 import numpy as np
 import pytest
 
@@ -214,3 +216,25 @@ def test_weakly_attached_pairs():
     assert determined_mask(g, 130.0, seeds=c["code"] == 1).all()
     # without the seed information the seeded background cluster looks trapped
     assert not determined_mask(g, 130.0).all()
+
+
+def test_poisson_weight_is_the_count_formula():
+    # Sec. III-C case study: w = exp(-(sqrt(n_p) - sqrt(n_q))^2 / 2) on raw
+    # counts; the oracle takes g = n / S with beta = S
+    S = 255.0
+    for na, nb in [(100, 100), (100, 81), (49, 64), (0, 9), (250, 30), (255, 0)]:
+        want = max(math.exp(-0.5 * (math.sqrt(na) - math.sqrt(nb)) ** 2), O.W_MIN)
+        got = O.weight(na / S, nb / S, S, kind="poisson")
+        assert abs(got - want) <= 1e-12 * want
+
+
+def test_poisson_voltage_divider():
+    # seed 0 -- free -- seed 1 on a 1 x 1 x 3 chain: x = w2 / (w1 + w2)
+    S = 255.0
+    n = np.array([16.0, 25.0, 49.0])
+    g = (n / S).reshape(1, 1, 3)
+    code = np.array([O.SEED, O.FREE, O.SEED], np.uint8).reshape(1, 1, 3)
+    xin = np.array([0.0, 0.0, 1.0]).reshape(1, 1, 3)
+    x, it, rr, st = O.rw_solve(g, code, xin, S, kind="poisson")
+    w1, w2 = math.exp(-0.5 * (4 - 5) ** 2), math.exp(-0.5 * (5 - 7) ** 2)
+    assert st == 0 and abs(x[0, 0, 1] - w2 / (w1 + w2)) <= 1e-12
