@@ -218,8 +218,28 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     return ok;
 }
 
-// waves = 0: enough z-chunks for two CTAs per resident slot; waves = k >= 1:
-// as many z-chunks as fill k whole waves of the persistent grid (no idle tail).
+// Even z-chunk depth that minimises the modelled sweep time: a work item
+// costs its planes plus a fixed pipeline fill and reduction (~5 plane steps),
+// items run in waves of `slots` resident CTAs, at most `max_items` items.
+int model_zc(int64_t per_plane, int nz, int64_t slots, int64_t max_items) {
+    int best_zc = nz + (nz & 1);
+    double best = 1e300;
+    for (int zc = 2;; zc += 2) {
+        const int64_t items = per_plane * ((nz + zc - 1) / zc);
+        if (items <= max_items) {
+            const double cost = (double)((items + slots - 1) / slots) * (zc + 5);
+            if (cost < best) {
+                best = cost;
+                best_zc = zc;
+            }
+        }
+        if (zc >= nz) break;
+    }
+    return best_zc;
+}
+
+// waves = 0: the z-chunking of the cost model (model_zc); waves = k >= 1: as
+// many z-chunks as fill k whole waves of the persistent grid.
 rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int ipg, SweepCfg* c, int waves = 0) {
     if (sweep_occupancy(fp64, gtype, tile) <= 0) {
         return fail(RW_ERR_INVALID_ARG, "sweep tile %d not available for this precision/storage", tile);
@@ -231,13 +251,15 @@ rw_status make_cfg(int fp64, int gtype, int tile, const Boxes& bx, int sms, int 
     c->ntx = (bx.nx + c->tx - 1) / c->tx;
     c->nty = (bx.ny + c->ty - 1) / c->ty;
     const int occ = std::max(1, sweep_occupancy(fp64, gtype, tile));
-    const int64_t want = (int64_t)2 * occ * sms;
     const int64_t per_plane = (int64_t)bx.nbox * c->ntx * c->nty;
     const int64_t slots = (int64_t)occ * sms;
-    int nzc = (int)std::max<int64_t>(1, (want + per_plane - 1) / per_plane);
-    if (waves > 0) nzc = (int)std::max<int64_t>(1, (waves * slots) / per_plane);
-    int zc = (bx.nz + nzc - 1) / nzc;
-    zc = std::max(zc, std::min(bx.nz, 8));
+    int zc;
+    if (waves > 0) {
+        const int nzc = (int)std::max<int64_t>(1, (waves * slots) / per_plane);
+        zc = std::max((bx.nz + nzc - 1) / nzc, std::min(bx.nz, 2));
+    } else {
+        zc = model_zc(per_plane, bx.nz, slots, INT64_MAX);
+    }
     zc = (zc + 1) & ~1;  // chunks start at even planes (the strip kernel's unrolled z loop)
     c->waves = waves;
     c->zc = zc;
@@ -328,10 +350,8 @@ void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, in
     const int occ = std::max(1, sweep_occupancy(fp64, gtype, full.tile));
     const int64_t slots = (int64_t)occ * sms;
     const int64_t per_plane = (int64_t)nact * full.ntx * full.nty;
-    int64_t nzc = std::max<int64_t>(full.nzc, (2 * slots + per_plane - 1) / per_plane);
-    nzc = std::min<int64_t>(nzc, std::max(1, (nz + 3) / 4));                       // chunks of >= 4 planes
-    nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, (int64_t)(part_elems / 6) / per_plane));  // partials fit
-    const int zc = ((int)((nz + nzc - 1) / nzc) + 1) & ~1;  // even, see make_cfg
+    // the partials buffer holds (part_elems / 6) items
+    const int zc = model_zc(per_plane, nz, slots, std::max<int64_t>((int64_t)(part_elems / 6), per_plane));
     c->zc = zc;
     c->nzc = (nz + zc - 1) / zc;
     c->grid = (int)std::max<int64_t>(1, std::min<int64_t>(per_plane * c->nzc, slots));
