@@ -273,25 +273,66 @@ cudaError_t launch_contract(const ContractArgs& a, cudaStream_t s) {
 // Level fill: voxels of absent nodes take the upsampled parent field (the
 // nearest transitive parent's values, Sec. IV-D1); reused nodes copy the old
 // field; solved nodes were written by k_contract.
+// One thread per 4 consecutive voxels of a row (grid: x quads and rows in
+// x / y, planes in z): the y / z taps and the parent values are shared by the
+// four voxels; each value is the same expression as upsample_at.
 __global__ void k_fill(const FillArgs a) {
-    const int64_t n = (int64_t)a.lx * a.ly * a.lz;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int X, Y, Z;
-    vox_xyz(i, a.lx, a.ly, n, &X, &Y, &Z);
-    const int64_t b = ((int64_t)(Z / a.s) * a.nby + (Y / a.s)) * a.nbx + (X / a.s);
-    const uint8_t st = a.status[b];
-    if (st == 1) return;
-    if (st == 2) {
-        a.field[i] = a.old[i];
-        return;
+    const int X0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Z = blockIdx.z;
+    if (X0 >= a.lx || Y >= a.ly) return;
+    const int64_t row = ((int64_t)Z * a.ly + Y) * a.lx;
+    float v[4];
+    bool wr[4];
+    const int bzy = (Z / a.s) * a.nby + (Y / a.s);
+    int ya = 0, yb = 0, za = 0, zb = 0;
+    float wya = 0.f, wyb = 0.f, wza = 0.f, wzb = 0.f;
+    if (a.parent) {
+        taps(Y, a.py, &ya, &yb, &wya, &wyb);
+        taps(Z, a.pz, &za, &zb, &wza, &wzb);
     }
-    a.field[i] = a.parent ? upsample_at(a.parent, a.px, a.py, a.pz, X, Y, Z) : 0.0f;
+    const int64_t sy = a.px, sz = (int64_t)a.px * a.py;
+    const float* Paa = a.parent + za * sz + ya * sy;
+    const float* Pab = a.parent + za * sz + yb * sy;
+    const float* Pba = a.parent + zb * sz + ya * sy;
+    const float* Pbb = a.parent + zb * sz + yb * sy;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int X = X0 + k;
+        wr[k] = false;
+        v[k] = 0.0f;
+        if (X >= a.lx) continue;
+        const uint8_t st = a.status[(int64_t)bzy * a.nbx + X / a.s];
+        if (st == 1) continue;
+        wr[k] = true;
+        if (st == 2) {
+            v[k] = a.old[row + X];
+        } else if (a.parent) {
+            int xa, xb;
+            float wxa, wxb;
+            taps(X, a.px, &xa, &xb, &wxa, &wxb);
+            const float c00 = wxa * Paa[xa] + wxb * Paa[xb];
+            const float c01 = wxa * Pab[xa] + wxb * Pab[xb];
+            const float c10 = wxa * Pba[xa] + wxb * Pba[xb];
+            const float c11 = wxa * Pbb[xa] + wxb * Pbb[xb];
+            v[k] = wza * (wya * c00 + wyb * c01) + wzb * (wya * c10 + wyb * c11);
+        }
+    }
+    float* out = a.field + row + X0;
+    if (wr[0] && wr[1] && wr[2] && wr[3] && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0)) {
+        *reinterpret_cast<float4*>(out) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (wr[k]) out[k] = v[k];
+    }
 }
 
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
-    const int64_t n = (int64_t)a.lx * a.ly * a.lz;
-    k_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    if ((int64_t)a.lx * a.ly * a.lz == 0) return cudaSuccess;
+    const dim3 blk(32, 8, 1);
+    const dim3 grid((unsigned)((a.lx + 127) / 128), (unsigned)((a.ly + 7) / 8), (unsigned)a.lz);
+    k_fill<<<grid, blk, 0, s>>>(a);
     return cudaGetLastError();
 }
 
