@@ -630,7 +630,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     RCK(ws_get_t(w, S_NACT, 64, &nact));
     int* list = nullptr;
     RCK(ws_get_t(w, S_LIST, (bx.nbox + 1) * sizeof(int), &list));
-    const int bpb = (int)((nvox + 255) / 256);
+    const int bpb = (int)((nvox + 1023) / 1024);  // k_residual: up to 4 voxels per thread
     RCK(ws_get_t(w, S_RPART, (size_t)bx.nbox * bpb * 4 * sizeof(double), &rpart));
     PrecState ps;
     RCK(prec_setup(w, P, o, cur64, &ps, &part));

@@ -162,10 +162,15 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
     const int box = blockIdx.y;
     const int nx = a.bx.nx, ny = a.bx.ny, nz = a.bx.nz;
     const int64_t nvox = (int64_t)nx * ny * nz;
-    const int64_t li = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    // up to 4 voxels per thread, a grid stride apart (blocks_per_box blocks
+    // per box): the FP64 reductions below are amortised over them
+    const int64_t li0 = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t stride = (int64_t)a.blocks_per_box * 256;
     double bb = 0, rr = 0;
     int ns = 0, nf = 0;
-    if (li < nvox) {
+    for (int rep = 0; rep < 4; ++rep) {
+        const int64_t li = li0 + rep * stride;
+        if (li >= nvox) break;
         int ex, ey, ez;
         box_extent(a.bx, box, &ex, &ey, &ez);
         int x, y, z;
@@ -177,9 +182,9 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
         T uo = 0;
         if (x < ex && y < ey && z < ez) {
             const uint8_t c = a.code[i];
-            if (c == SEED) ns = 1;
+            if (c == SEED) ++ns;
             if (c == FREE) {
-                nf = 1;
+                ++nf;
                 const double gi = gdbl_w(a, i), xi = xh[i];
                 const double rh = a.rhs ? (double)a.rhs[i] : 0.0;
                 double d = 0, s = 0, b = rh;
@@ -207,8 +212,8 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                     if (cj == SEED) b += w * xj;
                 }
                 const double r = rh - s;
-                bb = b * b;
-                rr = r * r;
+                bb += b * b;
+                rr += r * r;
                 // u is stored in T: for FP32 the quotient of the rounded
                 // operands is as accurate as the stored value
                 if constexpr (sizeof(T) == 4) uo = d > 0.0 ? (float)r / (float)d : 0.0f;
