@@ -573,9 +573,9 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
 }
 
 // Autotuner: on the first round of a new problem class, time 4 sweeps of
-// every candidate tile on the live state (real PCG iterations; an even count
-// keeps the buffer parity), keep the fastest and size the graph chunk to about
-// 1 ms of sweeps.
+// every candidate tile and z-chunking on the live state (real PCG iterations;
+// an even count keeps the buffer parity), keep the fastest and size the graph
+// chunk to about 4 ms of sweeps.
 rw_status autotune(DevWorkspace* w, const SolveProblem& P, PrecState* ps, const SweepArgs& sa, SolveResult* R) {
     float best = 1e30f;
     int best_tile = ps->cfg.tile, best_waves = 0;
@@ -604,9 +604,11 @@ rw_status autotune(DevWorkspace* w, const SolveProblem& P, PrecState* ps, const 
             }
         }
     }
+    // graph chunks of ~4 ms: one host round trip per chunk; sweeps past a
+    // system's convergence exit at once
     const float per = best / 4.0f;
-    int k = (int)std::lround(1.0 / std::max(per, 1e-4f));
-    k = std::max(8, std::min(64, k)) & ~1;
+    int k = (int)std::lround(4.0 / std::max(per, 1e-4f));
+    k = std::max(8, std::min(32, k)) & ~1;
     RCK(make_cfg(ps->fp64, P.gtype, best_tile, P.bx, w->sms, k, &ps->cfg, best_waves));
     g_tuned[ps->key] = Tuned{best_tile, k, best_waves};
     ps->tune = false;
