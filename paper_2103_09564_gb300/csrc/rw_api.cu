@@ -305,8 +305,9 @@ struct SolveResult {
 
 // TMA descriptors for a strip-sweep launch: the padded arrays as 3-D tensors
 // [PZ * nbox][PY][PX] of 4-byte words; boxes (TX + 2V) x (TY + 3) x 1 for u, p
-// and the g words, TX (V = 4) or TX + 2V (V = 2) x TY x 1 for delta.
-rw_status strip_maps(int tile, SweepArgs* sa) {
+// and the g words, TX (V = 4) or TX + 2V (V = 2) x TY x 1 for delta.  `loop`
+// adds the maps of u_out / p_out, read by the odd iterations of a looped sweep.
+rw_status strip_maps(int tile, SweepArgs* sa, bool loop = false) {
     if (tile < TILE_STRIP_FIRST) return RW_OK;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* fn = nullptr;
@@ -336,7 +337,8 @@ rw_status strip_maps(int tile, SweepArgs* sa) {
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     if (!enc(&sa->tm.u, sa->u_in, box_t) || !enc(&sa->tm.p, sa->p_in, box_t) || !enc(&sa->tm.g, sa->gc, box_t) ||
-        !enc(&sa->tm.x, sa->x, box_x))
+        !enc(&sa->tm.x, sa->x, box_x) ||
+        (loop && (!enc(&sa->tm.ua, sa->u_out, box_t) || !enc(&sa->tm.pa, sa->p_out, box_t))))
         return fail(RW_ERR_CUDA, "TMA descriptor encoding failed (tile %d, padded %d x %d x %d)", tile, sa->px, sa->py,
                     sa->pz);
     return RW_OK;
@@ -345,9 +347,9 @@ rw_status strip_maps(int tile, SweepArgs* sa) {
 // Configuration of a sweep over `nact` compacted systems: the z-splitting is
 // deepened so that the systems still iterating fill the GPU again.
 void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, int sms, size_t part_elems,
-                 SweepCfg* c) {
+                 SweepCfg* c, int occ_override = 0) {
     *c = full;
-    const int occ = std::max(1, sweep_occupancy(fp64, gtype, full.tile));
+    const int occ = occ_override > 0 ? occ_override : std::max(1, sweep_occupancy(fp64, gtype, full.tile));
     const int64_t slots = (int64_t)occ * sms;
     const int64_t per_plane = (int64_t)nact * full.ntx * full.nty;
     // the partials buffer holds (part_elems / 6) items
@@ -362,7 +364,14 @@ void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, in
 // the number of active systems has halved, the active ones are compacted into
 // a list (ascending) and the following sweeps visit only them, with a deeper
 // z-splitting: the slow systems of a batch then no longer run at the width
-// the whole batch was tiled for.
+// the whole batch was tiled for.  Once the work of one sweep fits a single
+// wave of resident CTAs of a tile with a looped variant, the sweeps run
+// looped instead: one cooperative launch iterates until the active count has
+// halved (grid barriers in place of kernel boundaries), then the host
+// compacts again.  n_active_dev holds {active count, error flag, 5 words of
+// grid-barrier state}.
+constexpr int kLoopIters = 512;
+
 rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, void* const u[2], void* const p[2],
                            int fp64, int gtype, int* n_active_dev, int n_act0, int* list_dev, size_t part_elems,
                            int64_t* sweeps, int64_t cap, double* ms_dev) {
@@ -371,6 +380,26 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     sa.nlist = nullptr;
     int n_cur = sa.bx.nbox;
     cudaGraphExec_t exec = nullptr;
+    const int occ_loop = fp64 ? 0 : sweep5_occupancy_loop(cfg0.tile);
+    bool loop = false;
+    int lpar = 0;  // buffer parity of the next looped launch
+    auto use_cfg = [&](const SweepCfg& c) {
+        cfg = c;
+        sa.ntx = cfg.ntx;
+        sa.nty = cfg.nty;
+        sa.nzc = cfg.nzc;
+        sa.zc = cfg.zc;
+    };
+    // switch to (or stay in) looped sweeps when n systems fit one wave
+    auto try_loop = [&](int n) -> bool {
+        if (occ_loop <= 0) return false;
+        SweepCfg c2;
+        compact_cfg(cfg0, fp64, gtype, sa.bx.nz, n, w->sms, part_elems, &c2, occ_loop);
+        if ((int64_t)n * c2.ntx * c2.nty * c2.nzc > (int64_t)occ_loop * w->sms) return false;
+        use_cfg(c2);
+        loop = true;
+        return true;
+    };
     auto capture = [&]() -> rw_status {
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
@@ -402,22 +431,19 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     auto compact = [&](int n_act) -> rw_status {
         if (!list_dev || sa.bx.nbox < 2 || n_act <= 0 || 2 * n_act > n_cur) return RW_OK;
         CK(counted(launch_compact_active(sa.sc, sa.bx.nbox, list_dev, list_dev + sa.bx.nbox, w->stream)));
-        SweepCfg c2;
-        compact_cfg(cfg0, fp64, gtype, sa.bx.nz, n_act, w->sms, part_elems, &c2);
-        cfg = c2;
-        sa.ntx = cfg.ntx;
-        sa.nty = cfg.nty;
-        sa.nzc = cfg.nzc;
-        sa.zc = cfg.zc;
         sa.list = list_dev;
         sa.nlist = list_dev + sa.bx.nbox;
         n_cur = n_act;
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
+        if (try_loop(n_act)) return RW_OK;
+        SweepCfg c2;
+        compact_cfg(cfg0, fp64, gtype, sa.bx.nz, n_act, w->sms, part_elems, &c2);
+        use_cfg(c2);
         return capture();
     };
     rw_status st = compact(n_act0);
-    if (st == RW_OK && !exec) st = capture();
+    if (st == RW_OK && !exec && !loop && !try_loop(n_cur)) st = capture();
     if (st != RW_OK) {
         if (exec) cudaGraphExecDestroy(exec);
         return st;
@@ -427,11 +453,29 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     CK(cudaEventCreate(&ev1));
     int n_act = 1;
     while (n_act > 0 && *sweeps < cap) {
-        cudaError_t e = cudaEventRecord(ev0, w->stream);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, w->stream);
+        int64_t done = cfg.ipg;
+        cudaError_t e = cudaSuccess;
+        if (loop) {
+            sa.u_in = u[lpar];
+            sa.p_in = p[lpar];
+            sa.u_out = u[lpar ^ 1];
+            sa.p_out = p[lpar ^ 1];
+            sa.parity = lpar;
+            sa.loop_iters = (int)std::min<int64_t>(kLoopIters, cap - *sweeps);
+            sa.loop_stop = list_dev && sa.bx.nbox >= 2 ? n_cur / 2 : 0;  // stop where compaction pays
+            sa.gsync = reinterpret_cast<unsigned*>(n_active_dev + 2);
+            st = strip_maps(cfg.tile, &sa, true);
+            if (st != RW_OK) break;
+            e = cudaMemsetAsync(sa.gsync, 0, 5 * sizeof(unsigned), w->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev0, w->stream);
+            if (e == cudaSuccess) e = sweep5_launch_loop(cfg.tile, sa, cfg.grid, w->stream);
+        } else {
+            e = cudaEventRecord(ev0, w->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, w->stream);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(ev1, w->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(w->pinned, n_active_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->stream);
+            e = cudaMemcpyAsync(w->pinned, n_active_dev, 7 * sizeof(int), cudaMemcpyDeviceToHost, w->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
@@ -441,11 +485,21 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
             break;
         }
         *ms_dev += ms;
-        *sweeps += cfg.ipg;
-        g_launches += cfg.ipg;
+        if (loop) {
+            done = w->pinned[6];  // iterations the looped launch completed
+            lpar = (int)((lpar + done) & 1);
+            g_launches += 1;
+        } else {
+            g_launches += cfg.ipg;
+        }
+        *sweeps += done;
         n_act = w->pinned[0];
         if (w->pinned[1]) {
-            st = fail(RW_ERR_CUDA, "PCG sweep: a load wait ran out (tile %d)", cfg.tile);
+            st = fail(RW_ERR_CUDA, "PCG sweep: a load or grid-barrier wait ran out (tile %d)", cfg.tile);
+            break;
+        }
+        if (done <= 0) {
+            st = fail(RW_ERR_CUDA, "PCG sweep: a looped launch completed no iteration (tile %d)", cfg.tile);
             break;
         }
         if (n_act > 0 && *sweeps < cap) {

@@ -44,6 +44,7 @@ struct Boxes {
 // delta), encoded by the host for the launch's buffers and tile.
 struct StripMaps {
     CUtensorMap u, p, g, x;
+    CUtensorMap ua, pa;  // u and p of the other parity (the looped sweep's odd iterations)
 };
 
 struct SweepArgs {
@@ -68,7 +69,10 @@ struct SweepArgs {
     float wminf;
     double mbeta;           // -beta, FP64 weights
     double wmin;
-    int* err = nullptr;     // set to 1 by a strip sweep whose load wait ran out
+    int* err = nullptr;     // set to 1 by a strip sweep whose load or grid wait ran out
+    int loop_iters = 1;     // looped strip sweep: PCG iterations per launch
+    int loop_stop = 0;      // looped strip sweep: stop once at most this many systems are active
+    unsigned* gsync = nullptr;  // looped strip sweep: {arrivals, generation, go[2], iterations done}
     int sqrt_g = 0;         // Poisson weights: FP64 sweep reads sqrt(g) (the g words are packed so)
     StripMaps tm;           // k_sweep5 only
 };
@@ -92,6 +96,10 @@ inline int tile_margin(int tile) {
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
 // combination that is not instantiated.
+// Looped strip sweep (cooperative launch, up to a.loop_iters iterations; brick
+// tiles only: cudaErrorInvalidValue otherwise) and its resident CTAs per SM.
+cudaError_t sweep5_launch_loop(int tile, const SweepArgs& a, int grid, cudaStream_t s);
+int sweep5_occupancy_loop(int tile);
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s);
 size_t sweep_smem_bytes(int fp64, int tile);
 void tile_dims(int tile, int* tx, int* ty);

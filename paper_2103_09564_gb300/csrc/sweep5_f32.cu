@@ -42,7 +42,52 @@ int occupancy_one() {
     return n;
 }
 
+template <int TX, int TY, int V, int NT, int D, int MB>
+cudaError_t launch_loop_one(const SweepArgs& a, int grid, cudaStream_t s) {
+    auto fn = k_sweep5<TX, TY, V, NT, D, MB, true>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweep5_smem_bytes<TX, TY, V, D>());
+    if (e != cudaSuccess) return e;
+    SweepArgs arg = a;
+    void* args[] = {&arg};
+    return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(NT), args, sweep5_smem_bytes<TX, TY, V, D>(),
+                                       s);
+}
+
+template <int TX, int TY, int V, int NT, int D, int MB>
+int occupancy_loop_one() {
+    int n = 0;
+    cudaFuncSetAttribute(k_sweep5<TX, TY, V, NT, D, MB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep5_smem_bytes<TX, TY, V, D>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, V, NT, D, MB, true>, NT,
+                                                  sweep5_smem_bytes<TX, TY, V, D>());
+    return n;
+}
+
 }  // namespace
+
+// Looped (multi-iteration, cooperative) strip sweep: the brick tiles only.
+cudaError_t sweep5_launch_loop(int tile, const SweepArgs& a, int grid, cudaStream_t s) {
+    switch (tile) {
+    case 24:
+        return launch_loop_one<40, 20, 4, 288, 2, 2>(a, grid, s);
+    case 25:
+        return launch_loop_one<40, 8, 4, 160, 2, 3>(a, grid, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+int sweep5_occupancy_loop(int tile) {
+    switch (tile) {
+    case 24:
+        return occupancy_loop_one<40, 20, 4, 288, 2, 2>();
+    case 25:
+        return occupancy_loop_one<40, 8, 4, 160, 2, 3>();
+    default:
+        return 0;
+    }
+}
 
 cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     switch (tile) {

@@ -30,6 +30,14 @@
 //   sets the error flag and the thread stops waiting (it still reaches every
 //   barrier, so the CTA finishes).
 //
+// LOOP = true (small work that fits one wave of resident CTAs, launched
+// cooperatively): one launch runs up to A.loop_iters PCG iterations,
+// swapping the (u, p) buffers and their TMA descriptors each iteration; a
+// grid barrier (arrival counter + generation word, bounded spin) separates
+// the iterations, and its last arrival publishes whether any system is
+// still active, so every CTA takes the same exit.  Per-system scalars are
+// read through L2 (other CTAs update them between iterations).
+//
 // Tile: TX x TY interior voxels (TX a multiple of V).  The thread grid covers
 // strips x = -V .. TX+V-1 (SX = TX/V + 2 strips) and rows y = -1 .. TY+1
 // (RY = TY + 3 rows): p_k is needed on x = -1 .. TX+1, y = -1 .. TY+1; u' on
@@ -138,6 +146,42 @@ __device__ __forceinline__ float wgt5(uint32_t a, uint32_t b, float c2, float wm
     return fmaxf(w, 0.0f);
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of iteration `it` of a looped sweep (thread 0 of each CTA
+// calls it after the CTA's work): returns whether the next iteration runs,
+// i.e. whether more than `stop` systems are still active.
+// g = {arrivals, generation, go[2], iterations done}.  A wait that runs out
+// sets *err and returns false.
+__device__ __forceinline__ bool grid_step(unsigned* g, int it, const int* n_active, int stop, int* err) {
+    __threadfence();
+    const unsigned target = gridDim.x * (unsigned)(it + 1);
+    const unsigned old = atomicAdd(&g[0], 1u);
+    if (old == target - 1u) {
+        __threadfence();  // the other CTAs' updates of n_active precede their arrivals
+        g[2 + (it & 1)] = (*(volatile const int*)n_active > stop) ? 1u : 0u;
+        g[4] = (unsigned)(it + 1);
+        __threadfence();
+        atomicExch(&g[1], (unsigned)(it + 1));
+    } else {
+        long long spin = 0;
+        while (ld_acquire_u32(&g[1]) < (unsigned)(it + 1)) {
+            if (++spin > (1LL << 24)) {
+                if (err) atomicExch(err, 1);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+    // the next iteration's TMA loads (async proxy) follow the acquired writes
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    return *(volatile const unsigned*)&g[2 + (it & 1)] != 0u;
+}
+
 // Per-strip registers carried from one plane to the next.
 template <int V>
 struct StripState {
@@ -147,7 +191,7 @@ struct StripState {
     float wzm[V];   // w(z-1, z)
 };
 
-template <int TX, int TY, int V, int NT, int D, int MINB>
+template <int TX, int TY, int V, int NT, int D, int MINB, bool LOOP = false>
 __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ SweepArgs A) {
     using L = Strip<TX, TY, V, D>;
     constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR;
@@ -226,12 +270,23 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
     __syncthreads();
     uint32_t seq = 0;      // planes issued by this CTA so far (the same in every thread)
     bool waited_out = false;
+    __shared__ int s_go;
+    using SP = typename std::conditional<LOOP, volatile BoxScalars*, BoxScalars*>::type;
+
+    for (int it = 0; it < (LOOP ? A.loop_iters : 1); ++it) {
+    // iteration `it` reads the (u, p) copy of parity A.parity + it
+    const bool odd = LOOP && (it & 1);
+    const CUtensorMap* mu = odd ? &A.tm.ua : &A.tm.u;
+    const CUtensorMap* mp = odd ? &A.tm.pa : &A.tm.p;
+    float* const u_out = static_cast<float*>(odd ? const_cast<void*>(A.u_in) : A.u_out);
+    float* const p_out = static_cast<float*>(odd ? const_cast<void*>(A.p_in) : A.p_out);
+    const int out_par = (A.parity + it + 1) & 1;
 
     for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
         const int li = (int)(w / tpb);  // position in the list of active systems
         const int box = A.list ? A.list[li] : li;
         const int t = (int)(w - (int64_t)li * tpb);
-        BoxScalars* S = A.sc + box;
+        SP S = A.sc + box;
         if (!S->active) continue;
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
         const float alpha = (float)S->alpha;
@@ -247,8 +302,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             // padded coordinates of this strip: x + V, y + 2, z + 2
             const int64_t base = (int64_t)box * bstride + (int64_t)(ty * TY + ry + 1) * PX + tx * TX + V * sx;
             float* Xb = static_cast<float*>(A.x) + base;
-            float* Uo = static_cast<float*>(A.u_out) + base;
-            float* Po = static_cast<float*>(A.p_out) + base;
+            float* Uo = u_out + base;
+            float* Po = p_out + base;
 
             // plane z of this work item is the CTA's load number q(z); it sits
             // in ring slot q % NR and completes phase (q / NR) & 1 of its mbarrier
@@ -266,8 +321,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 const bool wx = z >= z0 && z < z1;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_expect_tx(bar, (uint32_t)(3 * PL * 4 + (wx ? XW * TY * 4 : 0)));
-                tma_load3(sU + sl * PLA * 4, &A.tm.u, cx, cy, cz + z, bar);
-                tma_load3(sP + sl * PLA * 4, &A.tm.p, cx, cy, cz + z, bar);
+                tma_load3(sU + sl * PLA * 4, mu, cx, cy, cz + z, bar);
+                tma_load3(sP + sl * PLA * 4, mp, cx, cy, cz + z, bar);
                 tma_load3(sG + sl * PLA * 4, &A.tm.g, cx, cy, cz + z, bar);
                 if (wx) tma_load3(sX + sl * NIA * 4, &A.tm.x, cx + XC, cy + 1, cz + z, bar);
             };
@@ -435,7 +490,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
 #pragma unroll
             for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
-            const unsigned prev = atomicAdd(&S->counter, 1u);
+            const unsigned prev = atomicAdd(const_cast<unsigned*>(&S->counter), 1u);
             s_last = (prev == (unsigned)tpb - 1u);
         }
         __syncthreads();
@@ -449,10 +504,20 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             block_reduce<NT, 6>(tv, red);
             if (tid == 0) {
                 S->counter = 0u;
-                finalize_box(S, tv, A.n_active, A.parity ^ 1);
+                finalize_box(S, tv, A.n_active, out_par);
             }
         }
         __syncthreads();
+    }
+    if constexpr (LOOP) {
+        // this iteration's global writes become visible to the next one's
+        // TMA reads (async proxy) before the grid barrier releases them
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) s_go = grid_step(A.gsync, it, A.n_active, A.loop_stop, A.err) ? 1 : 0;
+        __syncthreads();
+        if (!s_go) break;
+    }
     }
 }
 

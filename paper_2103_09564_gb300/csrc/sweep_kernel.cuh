@@ -137,7 +137,8 @@ __device__ __forceinline__ void block_reduce_f32(const float* f, double* v, doub
 // the sweep's own inner products keeps them valid after the residual is
 // replaced by the FP64 one (the search direction survives the replacement).
 // out_par is the buffer index the sweep wrote.
-__device__ __forceinline__ void finalize_box(BoxScalars* S, const double* v, int* n_active, int out_par) {
+template <typename SP>  // BoxScalars* or volatile BoxScalars* (read through L2)
+__device__ __forceinline__ void finalize_box(SP S, const double* v, int* n_active, int out_par) {
     const double g = v[0], rr = v[1], dl = v[2], ep = v[3], pi = v[4], tau = v[5];
     bool stop;
     S->par = out_par;
