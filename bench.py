@@ -420,9 +420,9 @@ def run_multiclass(args):
     from three 200-voxel strokes per class; then each step adds one stroke of
     a random class: all three trees are updated (Sec. IV-E) and the argmax
     labels of the leaf are recomputed.  Default volume 1024 x 1024 x 2048
-    (x, y, z): the 2048 x 2048 x 4096 interaction workload at half size per
-    axis (three dense trees of the full size would need ~380 GB of leaf
-    fields)."""
+    (x, y, z); --n 2048 runs the full 2048 x 2048 x 4096 workload (three
+    trees of 78.5 GB, the pyramid 44 GB: batches of --max-batch bricks and
+    the leaf labels in pinned host memory keep it within HBM)."""
     import torch
     import paper_2103_09564_gb300 as rw
     import phantoms as P
@@ -433,12 +433,17 @@ def run_multiclass(args):
     t0 = time.perf_counter()
     c = P.multiclass_case(shape, seed=0, n_segments=200, n_blobs=400, n_updates=n_up, device=dev)
     t_phantom = time.perf_counter() - t0
+    torch.cuda.empty_cache()  # the library allocates outside torch's cache
     pyr = rw.rw_build_pyramid(c["volume"], s, lo=0.0, hi=5000.0, normalize=True)
     del c["volume"]
-    opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol, prune_hom=1, prune_dt=0)
+    torch.cuda.empty_cache()
+    kw = {"max_batch": args.max_batch} if args.max_batch else {}
+    opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol, prune_hom=1, prune_dt=0, **kw)
     trees = [rw.Tree(pyr, opts) for _ in range(3)]
     nvox = shape[0] * shape[1] * shape[2]
-    labels = torch.empty(shape, dtype=torch.uint8, device=dev)
+    labels_host = nvox > (1 << 32)
+    labels = (torch.empty(shape, dtype=torch.uint8, pin_memory=True) if labels_host
+              else torch.empty(shape, dtype=torch.uint8, device=dev))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k, t in enumerate(trees):
@@ -470,12 +475,29 @@ def run_multiclass(args):
             lat.append(e0.elapsed_time(e1))
     ms = float(np.sum(lat))
     vi = sum(x["voxel_iters"] for st in stats for x in st)
+    # sampled check of the leaf labels (every slab of a host output): the
+    # argmax of the three trees' own fields on 8 boxes of 32^3
+    rs = np.random.default_rng(0)
+    lab_np = labels.cpu().numpy() if not labels_host else labels.numpy()
+    n_chk = n_bad = 0
+    for _ in range(8):
+        z0, y0, x0 = (int(rs.integers(0, d - 32 + 1)) for d in shape)
+        box = [x0, y0, z0, x0 + 32, y0 + 32, z0 + 32]
+        f = np.stack([t.read_level(pyr.levels - 1, box=box) for t in trees])
+        ref = np.argmax(f, axis=0).astype(np.uint8)
+        got = lab_np[z0:z0 + 32, y0:y0 + 32, x0:x0 + 32]
+        n_chk += ref.size
+        n_bad += int(np.count_nonzero(ref != got))
     line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "labels_check": {"voxels": n_chk, "mismatches": n_bad, "how": "argmax of the trees' fields on 8 "
+                                                                              "random 32^3 leaf boxes"},
             "config": {"workload": f"incremental 3-class hierarchical random walker, {shape[2]} x {shape[1]} x "
                                    f"{shape[0]} uint16 (phantoms.multiclass_case, seed 0), brick {s}, hom pruning, "
-                                   f"tol {args.tol}; one step = one added stroke: 3 tree updates + argmax",
+                                   f"tol {args.tol}; one step = one added stroke: 3 tree updates + argmax"
+                                   + (" (leaf labels to pinned host memory)" if labels_host else "")
+                                   + (f", batches of {args.max_batch} bricks" if args.max_batch else ""),
                        "update_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                              "max": float(np.max(lat))},
                        "leaf_voxels_per_s": nvox / (float(np.median(lat)) / 1e3),
@@ -502,6 +524,7 @@ def main():
                          "hierarchy on 1024 x 1024 x 2048")
     ap.add_argument("--brick", type=int, default=32)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-batch", type=int, default=0, help="bricks per batched solve (0: library default)")
     ap.add_argument("--leaf-host", action="store_true",
                     help="hier: leaf level in mapped host memory (out-of-core placement)")
     ap.add_argument("--n", type=int, default=0,

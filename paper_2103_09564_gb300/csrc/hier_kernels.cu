@@ -220,6 +220,7 @@ cudaError_t launch_apply_labels(const Boxes& bx, const BrickJob* jobs, const Lab
 __global__ void __launch_bounds__(256) k_contract(const ContractArgs a) {
     const double* xs = a.x;
     const int box = blockIdx.x;
+    if (a.skip && a.skip[box]) return;  // uniform over the block
     const BrickJob J = a.jobs[box];
     const int s = a.s;
     const int bx0 = J.bx * s, by0 = J.by * s, bz0 = J.bz * s;
@@ -233,10 +234,10 @@ __global__ void __launch_bounds__(256) k_contract(const ContractArgs a) {
         const int px = X - J.rx0, py = Y - J.ry0, pz = Z - J.rz0;
         const float v = (float)xs[(int64_t)box * pstride + ((int64_t)pz * a.bx.ny + py) * a.bx.nx + px];
         const int64_t li = ((int64_t)Z * a.ly + Y) * a.lx + X;
-        a.field[li] = v;
+        if (a.old) md = fmaxf(md, fabsf(v - a.old[li]));  // read before the write below (in place)
+        if (!a.stats_only) a.field[li] = v;
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
-        if (a.old) md = fmaxf(md, fabsf(v - a.old[li]));
     }
     __shared__ float r[3][8];
 #pragma unroll
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(256) k_contract(const ContractArgs a) {
         r[2][wid] = md;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && a.stats) {
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
             mn = fminf(mn, r[0][k]);
             mx = fmaxf(mx, r[1][k]);
@@ -271,8 +272,9 @@ cudaError_t launch_contract(const ContractArgs& a, cudaStream_t s) {
 }
 
 // Level fill: voxels of absent nodes take the upsampled parent field (the
-// nearest transitive parent's values, Sec. IV-D1); reused nodes copy the old
-// field; solved nodes were written by k_contract.
+// nearest transitive parent's values, Sec. IV-D1).  The field is updated in
+// place: solved nodes were written by k_contract, reused nodes keep the
+// values of the previous pass.
 // One thread per 4 consecutive voxels of a row (grid: x quads and rows in
 // x / y, planes in z): the y / z taps and the parent values are shared by the
 // four voxels; each value is the same expression as upsample_at.
@@ -303,11 +305,9 @@ __global__ void k_fill(const FillArgs a) {
         v[k] = 0.0f;
         if (X >= a.lx) continue;
         const uint8_t st = a.status[(int64_t)bzy * a.nbx + X / a.s];
-        if (st == 1) continue;
+        if (st != 0) continue;
         wr[k] = true;
-        if (st == 2) {
-            v[k] = a.old[row + X];
-        } else if (a.parent) {
+        if (a.parent) {
             int xa, xb;
             float wxa, wxb;
             taps(X, a.px, &xa, &xb, &wxa, &wxb);

@@ -1124,9 +1124,7 @@ struct TreeLevel {
     int nbx = 1, nby = 1, nbz = 1;
     int64_t nb = 1;
     float* P = nullptr;      // filled field (device address)
-    float* Pold = nullptr;   // previous filled field (incremental pass)
-    void* P_host = nullptr;  // host allocations when the level lives in host memory
-    void* Pold_host = nullptr;
+    void* P_host = nullptr;  // host allocation when the level lives in host memory
     std::vector<int32_t> flags;
     std::vector<float> mn, mx, md;
     std::vector<uint8_t> status;  // 0 absent, 1 solved (new values), 2 reused (old values)
@@ -1295,7 +1293,7 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
         ga.px = k > 0 ? py->dims[k - 1][0] : 1;
         ga.py = k > 0 ? py->dims[k - 1][1] : 1;
         ga.pz = k > 0 ? py->dims[k - 1][2] : 1;
-        ga.init = t->update ? L.Pold : nullptr;
+        ga.init = t->update ? L.P : nullptr;  // warm start: the previous pass's field (in place)
         ga.g_out = pg;
         ga.code_out = pcode;
         ga.x_out = px;
@@ -1321,7 +1319,10 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
         ca.s = s;
         ca.x = px;
         ca.field = L.P;
-        ca.old = t->update ? L.Pold : nullptr;
+        // an incremental pass updates the field in place: statistics first
+        // (against the old values), then the bricks that are not similar
+        ca.old = t->update ? L.P : nullptr;
+        ca.stats_only = t->update ? 1 : 0;
         ca.lx = d[0];
         ca.ly = d[1];
         ca.lz = d[2];
@@ -1350,10 +1351,19 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
             L.mn[bi] = mn;
             L.mx[bi] = mx;
             L.md[bi] = md;
+            hfl[i] = (f & RW_NODE_SIMILAR) ? 1 : 0;  // similar bricks keep their old values
             if (st) {
                 st->bricks_solved += 1;
                 if (cfl) st->bricks_conflict += 1;
             }
+        }
+        if (t->update) {
+            CK(cudaMemcpyAsync(dflags, hfl.data(), nb * sizeof(int), cudaMemcpyHostToDevice, w->stream));
+            ca.old = nullptr;
+            ca.stats_only = 0;
+            ca.stats = nullptr;
+            ca.skip = dflags;
+            CK(counted(launch_contract(ca, w->stream)));
         }
     }
     return RW_OK;
@@ -1420,7 +1430,6 @@ rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
     fa.px = k > 0 ? py->dims[k - 1][0] : 1;
     fa.py = k > 0 ? py->dims[k - 1][1] : 1;
     fa.pz = k > 0 ? py->dims[k - 1][2] : 1;
-    fa.old = L.Pold;
     fa.status = dstatus;
     fa.nbx = L.nbx;
     fa.nby = L.nby;
@@ -1572,13 +1581,10 @@ rw_status rw_tree_create(const rw_pyramid* py, const rw_opts* opts_in, rw_tree**
         L.nb = (int64_t)L.nbx * L.nby * L.nbz;
         const int64_t n = (int64_t)d[0] * d[1] * d[2];
         const bool host = py->leaf_host && k == py->K;
-        void *p0 = nullptr, *p1 = nullptr;
+        void* p0 = nullptr;
         cudaError_t e = level_alloc(host, n * 4, &p0, &L.P_host);
         L.P = static_cast<float*>(p0);
-        if (e == cudaSuccess) e = level_alloc(host, n * 4, &p1, &L.Pold_host);
-        L.Pold = static_cast<float*>(p1);
         if (e == cudaSuccess) e = cudaMemset(L.P, 0, n * 4);
-        if (e == cudaSuccess) e = cudaMemset(L.Pold, 0, n * 4);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             rw_tree_free(t);
@@ -1638,10 +1644,6 @@ rw_status rw_update_seeds(rw_tree* t, const rw_labels* added, rw_stats* stats, v
     RCK(copy_labels(t, added, 1));
     DevWorkspace* w = nullptr;
     RCK(enter(&w, stream));
-    for (auto& L : t->L) {
-        std::swap(L.P, L.Pold);
-        std::swap(L.P_host, L.Pold_host);
-    }
     t->update = 1;
     t->resolve.clear();
     t->reused.clear();
@@ -1705,15 +1707,27 @@ rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_
         if (bb[a] < 0 || bb[a + 3] > d[a] || bb[a] > bb[a + 3]) return fail(RW_ERR_INVALID_ARG, "box outside level");
     DevWorkspace* w = nullptr;
     RCK(enter(&w, stream));
-    const int64_t n = (bb[3] - bb[0]) * (bb[4] - bb[1]) * (bb[5] - bb[2]);
-    uint8_t* lab = labels_out;
-    float* prob = prob_out;
+    // host outputs go through device staging buffers, a slab of z planes
+    // (at most 64 Mi voxels) at a time
+    const int64_t plane = (bb[3] - bb[0]) * (bb[4] - bb[1]);
     const bool lab_dev = is_device_ptr(labels_out), prob_dev = !prob_out || is_device_ptr(prob_out);
-    if (!lab_dev) RCK(ws_get_t(w, S_CODE, n, &lab));
-    if (!prob_dev) RCK(ws_get_t(w, S_OUT, n * 4, &prob));
-    CK(counted(launch_argmax(cf, d[0], d[1], bb, lab, prob, w->stream)));
-    if (!lab_dev) CK(cudaMemcpyAsync(labels_out, lab, n, cudaMemcpyDeviceToHost, w->stream));
-    if (!prob_dev) CK(cudaMemcpyAsync(prob_out, prob, n * 4, cudaMemcpyDeviceToHost, w->stream));
+    const int64_t nz = bb[5] - bb[2];
+    const int64_t slab = (lab_dev && prob_dev) ? std::max<int64_t>(nz, 1)
+                                               : std::max<int64_t>(1, ((int64_t)1 << 26) / std::max<int64_t>(plane, 1));
+    uint8_t* lab_st = nullptr;
+    float* prob_st = nullptr;
+    if (!lab_dev) RCK(ws_get_t(w, S_CODE, std::max<int64_t>(1, std::min(slab, nz) * plane), &lab_st));
+    if (!prob_dev) RCK(ws_get_t(w, S_OUT, std::max<int64_t>(1, std::min(slab, nz) * plane) * 4, &prob_st));
+    for (int64_t z0 = 0; z0 < nz; z0 += slab) {
+        const int64_t z1 = std::min(nz, z0 + slab);
+        const int64_t sb[6] = {bb[0], bb[1], bb[2] + z0, bb[3], bb[4], bb[2] + z1};
+        const int64_t off = z0 * plane, m = (z1 - z0) * plane;
+        uint8_t* lab = lab_dev ? labels_out + off : lab_st;
+        float* prob = prob_out ? (prob_dev ? prob_out + off : prob_st) : nullptr;
+        CK(counted(launch_argmax(cf, d[0], d[1], sb, lab, prob, w->stream)));
+        if (!lab_dev) CK(cudaMemcpyAsync(labels_out + off, lab_st, m, cudaMemcpyDeviceToHost, w->stream));
+        if (!prob_dev) CK(cudaMemcpyAsync(prob_out + off, prob_st, m * 4, cudaMemcpyDeviceToHost, w->stream));
+    }
     return leave(w);
 }
 
@@ -1734,7 +1748,6 @@ void rw_tree_free(rw_tree* t) {
     if (!t) return;
     for (auto& L : t->L) {
         level_free(L.P, L.P_host);
-        level_free(L.Pold, L.Pold_host);
     }
     delete t;
 }

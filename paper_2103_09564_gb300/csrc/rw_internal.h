@@ -242,10 +242,12 @@ struct ContractArgs {
     const BrickJob* jobs;
     int s;                 // brick size
     const double* x;       // pool solution (FP64)
-    float* field;          // level k field (written on the brick box)
-    const float* old;      // old level k field (nullable) for max |new - old|
+    float* field;          // level k field (written on the brick box unless stats_only or skip[box])
+    const float* old;      // old level k field (nullable) for max |new - old|; may equal field when stats_only
     int lx, ly, lz;
     float* stats;          // [nbox][3]: min, max, maxdiff
+    int stats_only = 0;    // 1: statistics only, the field is not written
+    const int* skip = nullptr;  // per box, nonzero: nothing is written (nullable)
 };
 cudaError_t launch_contract(const ContractArgs& a, cudaStream_t s);
 struct FillArgs {
@@ -253,8 +255,7 @@ struct FillArgs {
     int lx, ly, lz;
     const float* parent;    // level k-1 filled field (nullptr at root)
     int px, py, pz;
-    const float* old;       // old level-k field (for reused nodes)
-    const uint8_t* status;  // per brick: 0 absent (upsample), 1 solved (keep), 2 reused (copy old)
+    const uint8_t* status;  // per brick: 0 absent (upsample), 1 solved, 2 reused (both kept in place)
     int nbx, nby, nbz, s;
 };
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s);

@@ -491,7 +491,9 @@ def multiclass_case(shape=(128, 128, 128), seed=0, n_segments=40, n_blobs=60, st
 
     Classes: 0 background, 1 branching vessel tree (as in vessel_tree, radii
     scaled with the smallest dim), 2 cell blobs (random rotated ellipsoids,
-    semi-axes U(4, 15) scaled, vessels take precedence).  Intensities per
+    semi-axes U(4, 15) times min(max(4 m / 1024, 0.5), 4) for the smallest
+    dim m -- large enough to hold a 200-voxel stroke from m = 1024 on --
+    vessels take precedence).  Intensities per
     class N(800, 250), N(3000, 250), N(2000, 250) (sigma = 5 % of the window
     [0, 5000]), rounded to uint16.  Strokes: `strokes_per_class` polylines of
     `stroke_len` voxels inside each class, then `n_updates` further strokes
@@ -506,7 +508,7 @@ def multiclass_case(shape=(128, 128, 128), seed=0, n_segments=40, n_blobs=60, st
     sc = min(shape) / 1024.0
     for _ in range(n_blobs):
         c = np.array([st.uniform(0, nx), st.uniform(0, ny), st.uniform(0, nz)])
-        ax = np.array([st.uniform(4.0, 15.0) for _ in range(3)]) * max(sc * 4.0, 0.5)
+        ax = np.array([st.uniform(4.0, 15.0) for _ in range(3)]) * min(max(sc * 4.0, 0.5), 4.0)
         R = st.rotation()
         r = float(ax.max())
         lo = np.maximum(np.floor(c - r - 1).astype(int), 0)
