@@ -440,6 +440,7 @@ def run_multiclass(args):
     kw = {"max_batch": args.max_batch} if args.max_batch else {}
     opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol, prune_hom=1, prune_dt=0, **kw)
     trees = [rw.Tree(pyr, opts) for _ in range(3)]
+    free_after_trees = torch.cuda.mem_get_info(dev)[0] / 1e9
     nvox = shape[0] * shape[1] * shape[2]
     labels_host = nvox > (1 << 32)
     labels = (torch.empty(shape, dtype=torch.uint8, pin_memory=True) if labels_host
@@ -475,6 +476,13 @@ def run_multiclass(args):
             lat.append(e0.elapsed_time(e1))
     ms = float(np.sum(lat))
     vi = sum(x["voxel_iters"] for st in stats for x in st)
+    # one full-leaf argmax on its own (part of every step above)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record()
+    rw.trees_argmax(trees, out=labels)
+    eb.record()
+    torch.cuda.synchronize()
+    argmax_ms = ea.elapsed_time(eb)
     # sampled check of the leaf labels (every slab of a host output): the
     # argmax of the three trees' own fields on 8 boxes of 32^3
     rs = np.random.default_rng(0)
@@ -502,6 +510,9 @@ def run_multiclass(args):
                                              "max": float(np.max(lat))},
                        "leaf_voxels_per_s": nvox / (float(np.median(lat)) / 1e3),
                        "initial_solve_s": t_init, "phantom_s": t_phantom,
+                       "device_free_gb_after_trees": free_after_trees,
+                       "sweep_ms_per_update": float(np.mean([sum(x["ms_sweeps"] for x in st) for st in stats])),
+                       "argmax_ms": argmax_ms,
                        "bricks_resolved_per_update": float(np.mean([sum(x["bricks_solved"] for x in st)
                                                                     for st in stats]))},
             "gpu_launches": int(sum(x["launches"] for st in stats for x in st)), "clocks": clk.summary()}

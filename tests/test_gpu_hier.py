@@ -281,3 +281,92 @@ def test_poisson_weights_hierarchy_parity(rw):
     oo = hrw.Opts(brick_size=8, beta=S, weight="poisson")
     ot = hrw.run(levels, xyz, val, oo)
     _compare(rw, tree, ot, oo, 8)
+
+
+class _At:
+    """A sub-block indexed with the global coordinates of its level (the
+    oracle's node solve slices its inputs with level coordinates)."""
+
+    def __init__(self, a, off):
+        self.a, self.off = a, off
+
+    def __getitem__(self, sl):
+        return self.a[tuple(slice(s.start - o, s.stop - o) for s, o in zip(sl, self.off))]
+
+
+def test_vessel_tree_1024_sampled_bricks_and_properties(rw):
+    """The 1024^3 vessel-tree workload with brick 32, in the benchmark's launch
+    configuration (batched levels, autotuned tiles; bricks solved to 1e-11 as
+    in every hierarchy parity test).  Properties of the whole result: every
+    level within [0, 1] (maximum principle) and every label voxel of the leaf
+    exact where its leaf brick was solved (pruned bricks hold the upsampled
+    parent).  Sampled parity: leaf bricks equal the oracle's FP64 solve of the
+    same brick problem (Eqs. 2-3: expanded box, border seeds from the
+    upsampled parent) posed on the GPU's own parent level."""
+    import torch
+    dev = torch.device("cuda", 0)
+    s = 32
+    ph = P.vessel_tree(n=1024, seed=0, device=dev)
+    xyz = np.asarray(ph["labels_xyz"], dtype=np.float64)
+    val = np.asarray(ph["labels_value"], dtype=np.float32)
+    vol = ph["volume"]
+    pyr = rw.rw_build_pyramid(vol, s, lo=0.0, hi=5000.0, normalize=True)
+    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=1e-11))
+    tree.run(xyz, val)
+    K = pyr.levels - 1
+    for k in range(K + 1):
+        f = torch.empty(tuple(reversed(pyr.dims[k])), dtype=torch.float32, device=dev)
+        tree.read_level(k, out=f)
+        assert float(f.min()) >= -1e-6 and float(f.max()) <= 1.0 + 1e-6, k
+    shape = tuple(reversed(pyr.dims[K]))
+    seeds, conflicts = hrw.rasterize(xyz, val, K, K, shape)
+    fl, mn, mx, _ = tree.node_stats(K)
+    zyx = np.array([v for v in sorted(seeds) if fl[v[0] // s, v[1] // s, v[2] // s] & rw.RW_NODE_SOLVED],
+                   dtype=np.int64)
+    assert len(zyx) > 100
+    got = f[torch.from_numpy(zyx[:, 0]).to(dev), torch.from_numpy(zyx[:, 1]).to(dev),
+            torch.from_numpy(zyx[:, 2]).to(dev)].cpu().numpy()
+    assert np.array_equal(got, np.array([seeds[tuple(v)] for v in zyx], dtype=np.float32))
+    del f
+
+    solved = [tuple(int(v) for v in b) for b in np.argwhere(fl & rw.RW_NODE_SOLVED)]
+    assert len(solved) > 50
+    solved.sort(key=lambda b: -(mx[b] - mn[b]))
+    sample = solved[:2] + solved[len(solved) // 3:len(solved) // 3 + 1] + solved[2 * len(solved) // 3:][:1]
+    oo = hrw.Opts(brick_size=s, beta=130.0)
+    se, m_lo, m_hi = hrw.margins(s, oo.expand)
+    pdims = tuple(reversed(pyr.dims[K - 1]))
+    for b in sample:
+        box, reg = hrw._region(b, shape, s, se, m_lo, m_hi)
+        lo = [r[0] for r in reg]
+        hi = [r[1] for r in reg]
+        blk = vol[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]].cpu().to(torch.int32).numpy().astype(np.uint16)
+        q = O.quantize(blk, 0.0, 5000.0, True)
+        g = O.leaf_level(q)
+        # the parent sub-block with one voxel of margin: its trilinear upsample
+        # equals the whole level's on the region
+        p0 = [max(0, lo[a] // 2 - 1) for a in range(3)]
+        p1 = [min(pdims[a], (hi[a] + 1) // 2 + 1) for a in range(3)]
+        par = tree.read_level(K - 1, box=[p0[2], p0[1], p0[0], p1[2], p1[1], p1[0]]).astype(np.float64)
+        up = hrw.upsample(par, tuple(min(2 * p1[a], shape[a]) - 2 * p0[a] for a in range(3)))
+        Up = _At(up, [2 * p0[a] for a in range(3)])
+        out, box2, _, _, _, _ = hrw._solve_node(K, b, _At(g, lo), Up, Up, seeds, conflicts, oo, shape)
+        assert box2 == box
+        gpu = tree.read_level(K, box=[box[2][0], box[1][0], box[0][0], box[2][1], box[1][1], box[0][1]])
+        # determined voxels of the brick problem: its seeds are the border
+        # layer on faces inside the level and the label voxels
+        sd = np.zeros(g.shape, bool)
+        for a in range(3):
+            if lo[a] > 0:
+                sd[(slice(None),) * a + (0,)] = True
+            if hi[a] < shape[a]:
+                sd[(slice(None),) * a + (-1,)] = True
+        for (z, y, x) in seeds:
+            if lo[0] <= z < hi[0] and lo[1] <= y < hi[1] and lo[2] <= x < hi[2]:
+                sd[z - lo[0], y - lo[1], x - lo[2]] = True
+        det = determined_mask(g, 130.0, seeds=sd)
+        det = det[box[0][0] - lo[0]:box[0][1] - lo[0], box[1][0] - lo[1]:box[1][1] - lo[1],
+                  box[2][0] - lo[2]:box[2][1] - lo[2]]
+        assert det.mean() > 0.99
+        err = np.max(np.abs(gpu.astype(np.float64) - out)[det])
+        assert err <= TOL, f"brick {b}: max |gpu - oracle| = {err}"
