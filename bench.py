@@ -511,6 +511,8 @@ def run_multiclass(args):
                        "leaf_voxels_per_s": nvox / (float(np.median(lat)) / 1e3),
                        "initial_solve_s": t_init, "phantom_s": t_phantom,
                        "device_free_gb_after_trees": free_after_trees,
+                       "tree_ms_per_update": float(np.mean([sum(x["ms"] for x in st) for st in stats])),
+                       "pcg_loop_ms_per_update": float(np.mean([sum(x["ms_solve"] for x in st) for st in stats])),
                        "sweep_ms_per_update": float(np.mean([sum(x["ms_sweeps"] for x in st) for st in stats])),
                        "argmax_ms": argmax_ms,
                        "bricks_resolved_per_update": float(np.mean([sum(x["bricks_solved"] for x in st)

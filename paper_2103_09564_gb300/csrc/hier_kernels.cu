@@ -346,26 +346,52 @@ __global__ void k_read_box(const float* field, int lx, int ly, int x0, int y0, i
 }
 
 // Multi-class labels: argmax over the class fields of one level (ties: the
-// lowest class index) on a box of the level.
+// lowest class index) on a box of the level.  One thread per 4 consecutive
+// outputs (x fastest), stored as one 32-bit word (labels) and one 128-bit
+// word (probabilities) where aligned: the outputs may be page-locked host
+// memory, written across the host link.
 __global__ void k_argmax(const ClassFields f, int lx, int ly, int x0, int y0, int z0, int bx, int by, int bz,
                          uint8_t* labels, float* prob) {
     const int64_t n = (int64_t)bx * by * bz;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    const int64_t k0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (k0 >= n) return;
     int x, y, z;
-    vox_xyz(k, bx, by, n, &x, &y, &z);
-    const int64_t i = ((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x);
-    int best = 0;
-    float pb = f.P[0][i];
-    for (int c = 1; c < f.n; ++c) {
-        const float v = f.P[c][i];
-        if (v > pb) {
-            pb = v;
-            best = c;
+    vox_xyz(k0, bx, by, n, &x, &y, &z);
+    uint32_t lw = 0;
+    float pv[4] = {0.f, 0.f, 0.f, 0.f};
+    const int m = n - k0 < 4 ? (int)(n - k0) : 4;
+    for (int j = 0; j < m; ++j) {
+        const int64_t i = ((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x);
+        int best = 0;
+        float pb = f.P[0][i];
+        for (int c = 1; c < f.n; ++c) {
+            const float v = f.P[c][i];
+            if (v > pb) {
+                pb = v;
+                best = c;
+            }
+        }
+        lw |= (uint32_t)best << (8 * j);
+        pv[j] = pb;
+        if (++x == bx) {
+            x = 0;
+            if (++y == by) y = 0, ++z;
         }
     }
-    labels[k] = (uint8_t)best;
-    if (prob) prob[k] = pb;
+    uint8_t* lo = labels + k0;
+    if (m == 4 && (reinterpret_cast<uintptr_t>(lo) & 3u) == 0) {
+        *reinterpret_cast<uint32_t*>(lo) = lw;
+    } else {
+        for (int j = 0; j < m; ++j) lo[j] = (uint8_t)(lw >> (8 * j));
+    }
+    if (prob) {
+        float* po = prob + k0;
+        if (m == 4 && (reinterpret_cast<uintptr_t>(po) & 15u) == 0) {
+            *reinterpret_cast<float4*>(po) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        } else {
+            for (int j = 0; j < m; ++j) po[j] = pv[j];
+        }
+    }
 }
 
 cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t box[6], uint8_t* labels, float* prob,
@@ -373,8 +399,9 @@ cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t bo
     const int bx = (int)(box[3] - box[0]), by = (int)(box[4] - box[1]), bz = (int)(box[5] - box[2]);
     const int64_t n = (int64_t)bx * by * bz;
     if (n == 0) return cudaSuccess;
-    k_argmax<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, lx, ly, (int)box[0], (int)box[1], (int)box[2], bx, by, bz,
-                                                          labels, prob);
+    const int64_t nt = (n + 3) / 4;
+    k_argmax<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(f, lx, ly, (int)box[0], (int)box[1], (int)box[2], bx, by,
+                                                           bz, labels, prob);
     return cudaGetLastError();
 }
 

@@ -132,6 +132,18 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked (pinned or registered) host memory, which
+// kernels can write directly; nullptr for other pointers.
+void* pinned_device_alias(void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Device view of a caller array: the pointer itself, or a staged copy.
 rw_status stage_in(DevWorkspace* w, int slot, const void* p, size_t bytes, const void** out) {
     if (!p) {
@@ -1707,10 +1719,15 @@ rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_
         if (bb[a] < 0 || bb[a + 3] > d[a] || bb[a] > bb[a + 3]) return fail(RW_ERR_INVALID_ARG, "box outside level");
     DevWorkspace* w = nullptr;
     RCK(enter(&w, stream));
-    // host outputs go through device staging buffers, a slab of z planes
-    // (at most 64 Mi voxels) at a time
+    // device and page-locked host outputs are written by the kernel; other
+    // host outputs go through device staging buffers, a slab of z planes (at
+    // most 64 Mi voxels) at a time
     const int64_t plane = (bb[3] - bb[0]) * (bb[4] - bb[1]);
-    const bool lab_dev = is_device_ptr(labels_out), prob_dev = !prob_out || is_device_ptr(prob_out);
+    uint8_t* lab_w = labels_out;  // kernel-writable address of the output (or nullptr)
+    float* prob_w = prob_out;
+    if (!is_device_ptr(labels_out)) lab_w = static_cast<uint8_t*>(pinned_device_alias(labels_out));
+    if (prob_out && !is_device_ptr(prob_out)) prob_w = static_cast<float*>(pinned_device_alias(prob_out));
+    const bool lab_dev = lab_w != nullptr, prob_dev = !prob_out || prob_w != nullptr;
     const int64_t nz = bb[5] - bb[2];
     const int64_t slab = (lab_dev && prob_dev) ? std::max<int64_t>(nz, 1)
                                                : std::max<int64_t>(1, ((int64_t)1 << 26) / std::max<int64_t>(plane, 1));
@@ -1722,8 +1739,8 @@ rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_
         const int64_t z1 = std::min(nz, z0 + slab);
         const int64_t sb[6] = {bb[0], bb[1], bb[2] + z0, bb[3], bb[4], bb[2] + z1};
         const int64_t off = z0 * plane, m = (z1 - z0) * plane;
-        uint8_t* lab = lab_dev ? labels_out + off : lab_st;
-        float* prob = prob_out ? (prob_dev ? prob_out + off : prob_st) : nullptr;
+        uint8_t* lab = lab_dev ? lab_w + off : lab_st;
+        float* prob = prob_out ? (prob_dev ? prob_w + off : prob_st) : nullptr;
         CK(counted(launch_argmax(cf, d[0], d[1], sb, lab, prob, w->stream)));
         if (!lab_dev) CK(cudaMemcpyAsync(labels_out + off, lab_st, m, cudaMemcpyDeviceToHost, w->stream));
         if (!prob_dev) CK(cudaMemcpyAsync(prob_out + off, prob_st, m * 4, cudaMemcpyDeviceToHost, w->stream));

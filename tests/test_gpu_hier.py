@@ -265,6 +265,38 @@ def test_argmax_ties_take_the_lowest_class(rw):
         rw.trees_argmax(trees, box=[0, 0, 0, 999, 1, 1])
 
 
+def test_argmax_output_kinds_agree(rw):
+    # pageable host memory (staged), device memory and page-locked host memory
+    # (written by the kernel) give the same labels and probabilities, on the
+    # whole leaf and on a box whose voxel count is not a multiple of 4
+    import torch
+    shape = (64, 48, 40)
+    c = P.multiclass_case(shape, seed=2, n_segments=12, n_blobs=12, n_updates=0)
+    pyr, trees = _class_trees(rw, c, 8, 1e-10, prune=True)
+    lab, prob = rw.trees_argmax(trees, prob=np.empty(shape, np.float32))
+    fields = np.stack([t.read_level(pyr.levels - 1) for t in trees])
+    assert np.array_equal(lab, np.argmax(fields, axis=0).astype(np.uint8))
+    assert np.array_equal(prob, fields.max(axis=0))
+    box = [3, 5, 7, 34, 38, 45]  # x0, y0, z0, x1, y1, z1: 31 x 33 x 38 voxels
+    sub = (slice(box[2], box[5]), slice(box[1], box[4]), slice(box[0], box[3]))
+    bshape = (box[5] - box[2], box[4] - box[1], box[3] - box[0])
+    assert np.prod(bshape) % 4 != 0
+    for b, shp, ref_l, ref_p in ((None, shape, lab, prob), (box, bshape, lab[sub], prob[sub])):
+        for kind in ("cuda", "pinned", "numpy"):
+            if kind == "numpy":
+                o, p = np.empty(shp, np.uint8), np.empty(shp, np.float32)
+            else:
+                kw = {"device": "cuda"} if kind == "cuda" else {"pin_memory": True}
+                o = torch.empty(shp, dtype=torch.uint8, **kw)
+                p = torch.empty(shp, dtype=torch.float32, **kw)
+            rw.trees_argmax(trees, box=b, out=o, prob=p)
+            torch.cuda.synchronize()
+            o = o.cpu().numpy() if kind != "numpy" else o
+            p = p.cpu().numpy() if kind != "numpy" else p
+            assert np.array_equal(o, ref_l), (kind, b)
+            assert np.array_equal(p, ref_p), (kind, b)
+
+
 def test_poisson_weights_hierarchy_parity(rw):
     S = 255.0
     c = P.poisson_ball(n=64, seed=5)
