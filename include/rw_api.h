@@ -59,7 +59,11 @@ enum { RW_CODE_FREE = 0, RW_CODE_SEED = 1, RW_CODE_ABSENT = 2 };
 enum {
     RW_NODE_SOLVED = 1, RW_NODE_PRUNABLE = 2, RW_NODE_HOM = 4, RW_NODE_DT = 8,
     RW_NODE_CFL = 16, RW_NODE_SIMILAR = 32, RW_NODE_REUSED = 64, RW_NODE_CFL_ADDED = 128,
-    RW_NODE_NO_SEEDS = 256
+    RW_NODE_NO_SEEDS = 256,
+    /* the node's values changed in the pass: re-solved and not similar, or
+     * absent and filled from a parent footprint that changed (every node of a
+     * full refinement) */
+    RW_NODE_CHANGED = 512
 };
 
 /* Intensity volume.  Normalisation (a reading: the paper applies
@@ -287,6 +291,18 @@ rw_status rw_update_seeds(rw_tree* tree, const rw_labels* added, rw_stats* stats
 #define RW_MAX_CLASSES 8
 rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_t level, const int64_t box[6],
                           uint8_t* labels_out, float* prob_out, void* stream);
+
+/* Multi-class labels after an incremental round (Sec. IV-E): rw_trees_argmax
+ * over the whole leaf level, recomputed only on the leaf bricks that changed
+ * (RW_NODE_CHANGED) in the latest pass of at least one tree; every other
+ * voxel of labels_out / prob_out keeps its contents.  Call it after each
+ * round in which every tree ran one pass (rw_update_seeds or a full
+ * refinement), on outputs holding the previous round's labels.  Outputs:
+ * device or page-locked host memory, the leaf level's layout (x fastest);
+ * RW_ERR_INVALID_ARG for other memory, a bad count, unrefined trees or trees
+ * on different pyramids. */
+rw_status rw_trees_argmax_changed(const rw_tree* const* trees, int32_t n_classes, uint8_t* labels_out,
+                                  float* prob_out, void* stream);
 
 /* Copy box [x0,x1) x [y0,y1) x [z0,z1) (box = {x0,y0,z0,x1,y1,z1}) of the
  * filled probability field of `level` to `out` (x fastest). */

@@ -19,11 +19,12 @@ import numpy as np
 
 from . import _abi
 from ._abi import (RW_CODE_ABSENT, RW_CODE_FREE, RW_CODE_SEED, RW_FP64, RW_MIXED, RW_NODE_CFL,  # noqa: F401
-                   RW_NODE_CFL_ADDED, RW_NODE_DT, RW_NODE_HOM, RW_NODE_NO_SEEDS, RW_NODE_PRUNABLE, RW_NODE_REUSED,
+                   RW_NODE_CFL_ADDED, RW_NODE_CHANGED, RW_NODE_DT, RW_NODE_HOM, RW_NODE_NO_SEEDS, RW_NODE_PRUNABLE,
+                   RW_NODE_REUSED,
                    RW_NODE_SIMILAR, RW_NODE_SOLVED, RW_STORE_F32, RW_STORE_UNORM16, LibraryMissing)
 
 __all__ = ["RWError", "Opts", "rw_solve", "rw_solve_noalloc", "rw_solve_adjoint", "rw_build_pyramid", "Pyramid", "Tree",
-           "trees_argmax", "load",
+           "trees_argmax", "trees_argmax_changed", "load",
            "release_workspace", "version"]
 
 
@@ -283,6 +284,22 @@ def trees_argmax(trees, level=None, box=None, out=None, prob=None):
     arr = (ctypes.c_void_p * len(trees))(*[t.h.value for t in trees])
     _check(load().rw_trees_argmax(arr, len(trees), level, b.ctypes.data, o.ptr, p.ptr if p else None,
                                   _stream(o, *( [p] if p else []))))
+    return o.obj, (p.obj if p else None)
+
+
+def trees_argmax_changed(trees, out, prob=None):
+    """After a round in which every tree ran one pass (update_seeds or run),
+    recompute the leaf labels in `out` (and the winning probability in
+    `prob`) on the leaf bricks that changed in any tree; the rest of `out`
+    keeps the previous round's labels.  `out` / `prob`: CUDA tensors or
+    page-locked (pinned) host tensors with the leaf level's shape."""
+    if not 2 <= len(trees) <= RW_MAX_CLASSES:
+        raise ValueError(f"need 2..{RW_MAX_CLASSES} trees")
+    o = _Arr(out)
+    p = _Arr(prob) if prob is not None else None
+    arr = (ctypes.c_void_p * len(trees))(*[t.h.value for t in trees])
+    _check(load().rw_trees_argmax_changed(arr, len(trees), o.ptr, p.ptr if p else None,
+                                          _stream(o, *([p] if p else []))))
     return o.obj, (p.obj if p else None)
 
 

@@ -16,7 +16,7 @@ RW_STORE_UNORM16, RW_STORE_F32 = 0, 1
 RW_MIXED, RW_FP64 = 0, 1
 RW_CODE_FREE, RW_CODE_SEED, RW_CODE_ABSENT = 0, 1, 2
 RW_NODE_SOLVED, RW_NODE_PRUNABLE, RW_NODE_HOM, RW_NODE_DT, RW_NODE_CFL, RW_NODE_SIMILAR, RW_NODE_REUSED, \
-    RW_NODE_CFL_ADDED, RW_NODE_NO_SEEDS = 1, 2, 4, 8, 16, 32, 64, 128, 256
+    RW_NODE_CFL_ADDED, RW_NODE_NO_SEEDS, RW_NODE_CHANGED = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
 RW_NOALLOC_MAX_VOXELS = 262144
 RW_NOALLOC_MAX_BATCH = 64
 RW_TILE = {"auto": 0, "32x16": 1, "64x8": 2, "40x8": 3, "40x20": 4, "80x8": 5, "80x16": 6, "32x8": 7, "32x32": 8,
@@ -30,7 +30,7 @@ EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspa
            "rw_solve_adjoint",
            "rw_build_pyramid", "rw_build_pyramid_ex", "rw_pyramid_info", "rw_pyramid_read_level", "rw_pyramid_free", "rw_tree_create",
            "rw_refine_level", "rw_update_seeds", "rw_tree_read_level", "rw_tree_node_stats", "rw_tree_free",
-           "rw_trees_argmax"]
+           "rw_trees_argmax", "rw_trees_argmax_changed"]
 
 
 class rw_volume(ctypes.Structure):
@@ -83,6 +83,7 @@ PROTOTYPES = {
                                         ctypes.POINTER(rw_opts), _P, _P, _P, _P, ctypes.POINTER(rw_stats), _P]),
     "rw_build_pyramid": (ctypes.c_int, [ctypes.POINTER(rw_volume), ctypes.c_int32, ctypes.POINTER(_P), _P]),
     "rw_trees_argmax": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
+    "rw_trees_argmax_changed": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P]),
     "rw_build_pyramid_ex": (ctypes.c_int, [ctypes.POINTER(rw_volume), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P),
                                            _P]),
     "rw_pyramid_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), _P]),

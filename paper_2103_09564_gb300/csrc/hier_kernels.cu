@@ -276,47 +276,51 @@ cudaError_t launch_contract(const ContractArgs& a, cudaStream_t s) {
 // place: solved nodes were written by k_contract, reused nodes keep the
 // values of the previous pass.
 // One thread per 4 consecutive voxels of a row (grid: x quads and rows in
-// x / y, planes in z): the y / z taps and the parent values are shared by the
-// four voxels; each value is the same expression as upsample_at.
+// x / y, planes in z).  Children 4q .. 4q+3 of a row read parent columns
+// 2q-1 .. 2q+2 (clamped); each column is interpolated in y, then z, and the
+// children combine two columns with weights 1/4, 3/4 (the taps of
+// upsample_at, applied axis by axis).
 __global__ void k_fill(const FillArgs a) {
-    const int X0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int X0 = 4 * q;
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int Z = blockIdx.z;
     if (X0 >= a.lx || Y >= a.ly) return;
     const int64_t row = ((int64_t)Z * a.ly + Y) * a.lx;
-    float v[4];
+    const uint8_t* strow = a.status + (int64_t)((Z / a.s) * a.nby + (Y / a.s)) * a.nbx;
     bool wr[4];
-    const int bzy = (Z / a.s) * a.nby + (Y / a.s);
-    int ya = 0, yb = 0, za = 0, zb = 0;
-    float wya = 0.f, wyb = 0.f, wza = 0.f, wzb = 0.f;
+    if ((a.s & 3) == 0) {  // the quad lies in one brick
+        const bool w = strow[X0 / a.s] == 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wr[k] = w && X0 + k < a.lx;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wr[k] = X0 + k < a.lx && strow[(X0 + k) / a.s] == 0;
+    }
+    if (!(wr[0] || wr[1] || wr[2] || wr[3])) return;
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (a.parent) {
+        int ya, yb, za, zb;
+        float wya, wyb, wza, wzb;
         taps(Y, a.py, &ya, &yb, &wya, &wyb);
         taps(Z, a.pz, &za, &zb, &wza, &wzb);
-    }
-    const int64_t sy = a.px, sz = (int64_t)a.px * a.py;
-    const float* Paa = a.parent + za * sz + ya * sy;
-    const float* Pab = a.parent + za * sz + yb * sy;
-    const float* Pba = a.parent + zb * sz + ya * sy;
-    const float* Pbb = a.parent + zb * sz + yb * sy;
+        const int64_t sy = a.px, sz = (int64_t)a.px * a.py;
+        const float* Paa = a.parent + za * sz + ya * sy;
+        const float* Pab = a.parent + za * sz + yb * sy;
+        const float* Pba = a.parent + zb * sz + ya * sy;
+        const float* Pbb = a.parent + zb * sz + yb * sy;
+        float c[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int X = X0 + k;
-        wr[k] = false;
-        v[k] = 0.0f;
-        if (X >= a.lx) continue;
-        const uint8_t st = a.status[(int64_t)bzy * a.nbx + X / a.s];
-        if (st != 0) continue;
-        wr[k] = true;
-        if (a.parent) {
-            int xa, xb;
-            float wxa, wxb;
-            taps(X, a.px, &xa, &xb, &wxa, &wxb);
-            const float c00 = wxa * Paa[xa] + wxb * Paa[xb];
-            const float c01 = wxa * Pab[xa] + wxb * Pab[xb];
-            const float c10 = wxa * Pba[xa] + wxb * Pba[xb];
-            const float c11 = wxa * Pbb[xa] + wxb * Pbb[xb];
-            v[k] = wza * (wya * c00 + wyb * c01) + wzb * (wya * c10 + wyb * c11);
+        for (int k = 0; k < 4; ++k) {
+            const int j = min(max(2 * q - 1 + k, 0), a.px - 1);
+            const float ca = fmaf(wya, Paa[j], wyb * Pab[j]);  // z = za
+            const float cb = fmaf(wya, Pba[j], wyb * Pbb[j]);  // z = zb
+            c[k] = fmaf(wza, ca, wzb * cb);
         }
+        v[0] = fmaf(0.25f, c[0], 0.75f * c[1]);
+        v[1] = fmaf(0.75f, c[1], 0.25f * c[2]);
+        v[2] = fmaf(0.25f, c[1], 0.75f * c[2]);
+        v[3] = fmaf(0.75f, c[2], 0.25f * c[3]);
     }
     float* out = a.field + row + X0;
     if (wr[0] && wr[1] && wr[2] && wr[3] && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0)) {
@@ -402,6 +406,62 @@ cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t bo
     const int64_t nt = (n + 3) / 4;
     k_argmax<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(f, lx, ly, (int)box[0], (int)box[1], (int)box[2], bx, by,
                                                            bz, labels, prob);
+    return cudaGetLastError();
+}
+
+// Argmax on a list of bricks: block (brick, plane of the brick), each thread
+// 4 consecutive voxels of a row (as k_argmax), outputs in the level's layout.
+__global__ void k_argmax_nodes(const ClassFields f, int lx, int ly, int lz, int s, int nbx, int nby,
+                               const int64_t* nodes, uint8_t* labels, float* prob) {
+    const int64_t nd = nodes[blockIdx.x];
+    const int bx = (int)(nd % nbx), by = (int)((nd / nbx) % nby), bz = (int)(nd / ((int64_t)nbx * nby));
+    const int Z = bz * s + (int)blockIdx.y;
+    if (Z >= lz) return;
+    const int qr = (s + 3) / 4;  // quads per brick row
+    for (int t = threadIdx.x; t < qr * s; t += blockDim.x) {
+        const int y = t / qr, xq = 4 * (t - y * qr);
+        const int Y = by * s + y, X0 = bx * s + xq;
+        if (Y >= ly || X0 >= lx) continue;
+        const int m = min(4, min(s - xq, lx - X0));
+        const int64_t i0 = ((int64_t)Z * ly + Y) * lx + X0;
+        uint32_t lw = 0;
+        float pv[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = 0; j < m; ++j) {
+            int best = 0;
+            float pb = f.P[0][i0 + j];
+            for (int c = 1; c < f.n; ++c) {
+                const float v = f.P[c][i0 + j];
+                if (v > pb) {
+                    pb = v;
+                    best = c;
+                }
+            }
+            lw |= (uint32_t)best << (8 * j);
+            pv[j] = pb;
+        }
+        uint8_t* lo = labels + i0;
+        if (m == 4 && (reinterpret_cast<uintptr_t>(lo) & 3u) == 0) {
+            *reinterpret_cast<uint32_t*>(lo) = lw;
+        } else {
+            for (int j = 0; j < m; ++j) lo[j] = (uint8_t)(lw >> (8 * j));
+        }
+        if (prob) {
+            float* po = prob + i0;
+            if (m == 4 && (reinterpret_cast<uintptr_t>(po) & 15u) == 0) {
+                *reinterpret_cast<float4*>(po) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            } else {
+                for (int j = 0; j < m; ++j) po[j] = pv[j];
+            }
+        }
+    }
+}
+
+cudaError_t launch_argmax_nodes(const ClassFields& f, int lx, int ly, int lz, int s, int nbx, int nby,
+                                const int64_t* nodes, int64_t n_nodes, uint8_t* labels, float* prob, cudaStream_t st) {
+    if (n_nodes == 0) return cudaSuccess;
+    if (n_nodes > 0x7fffffff || s > 65535) return cudaErrorInvalidValue;
+    k_argmax_nodes<<<dim3((unsigned)n_nodes, (unsigned)s), 256, 0, st>>>(f, lx, ly, lz, s, nbx, nby, nodes, labels,
+                                                                         prob);
     return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ double now_ms() {
 enum Slot {
     S_G, S_U0, S_U1, S_P0, S_P1, S_DELTA, S_XHI, S_PART, S_RPART, S_SC, S_NACT, S_VOL, S_CODE, S_VAL, S_X0, S_OUT,
     S_RHS, S_EXT, S_JOBS, S_LAB, S_BFLAGS, S_STATS, S_POOL_G, S_POOL_CODE, S_POOL_X, S_ADJ_PART, S_DBETA, S_DG,
-    S_XF, S_STATUS, S_GC, S_LIST, S_W64, S_COUNT
+    S_XF, S_STATUS, S_GC, S_LIST, S_W64, S_NODES, S_COUNT
 };
 
 struct DevWorkspace {
@@ -1140,6 +1140,8 @@ struct TreeLevel {
     std::vector<int32_t> flags;
     std::vector<float> mn, mx, md;
     std::vector<uint8_t> status;  // 0 absent, 1 solved (new values), 2 reused (old values)
+    std::vector<uint8_t> filled;  // 1: the values came from the level fill in the last pass
+    std::vector<uint8_t> changed; // 1: the values changed in the last pass
 };
 
 }  // namespace
@@ -1381,6 +1383,26 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
     return RW_OK;
 }
 
+// Whether a level-(k-1) node read by the trilinear upsample of node b of
+// level k (parent voxels h-1 .. h+1 around h = X / 2, clamped) changed in the
+// current pass.
+bool parent_changed(const rw_tree* t, int k, const std::array<int, 3>& b) {
+    const rw_pyramid* py = t->pyr;
+    const int s = py->s;
+    const TreeLevel& P = t->L[k - 1];
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        const int x0 = b[a] * s, x1 = std::min(x0 + s, py->dims[k][a]) - 1;
+        lo[a] = std::max(0, (x0 >> 1) - 1) / s;
+        hi[a] = std::min(py->dims[k - 1][a] - 1, (x1 >> 1) + 1) / s;
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x)
+                if (P.changed[((int64_t)z * P.nby + y) * P.nbx + x]) return true;
+    return false;
+}
+
 rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
     const rw_pyramid* py = t->pyr;
     TreeLevel& L = t->L[k];
@@ -1430,9 +1452,31 @@ rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
         if (k < py->K) children(t, k, b, &nreu);
         if (st) st->bricks_reused += 1;
     }
+    // Values that change in this pass: re-solved nodes that are not similar,
+    // and absent nodes, except those filled last pass from a parent footprint
+    // that has not changed (their values equal the new upsample).  The fill
+    // writes only the absent nodes that change (fill status 0).
+    std::vector<uint8_t> fst(L.nb);
+    for (int64_t i = 0; i < L.nb; ++i) {
+        bool ch;
+        if (L.status[i] == 1) {
+            ch = true;
+        } else if (L.status[i] == 2) {
+            ch = false;
+        } else if (!t->update || !L.filled[i] || k == 0) {
+            ch = true;
+        } else {
+            const std::array<int, 3> b = {(int)(i % L.nbx), (int)((i / L.nbx) % L.nby), (int)(i / ((int64_t)L.nbx * L.nby))};
+            ch = parent_changed(t, k, b);
+        }
+        L.changed[i] = ch;
+        if (ch) L.flags[i] |= RW_NODE_CHANGED;
+        fst[i] = (L.status[i] == 0 && ch) ? 0 : 1;
+        L.filled[i] = L.status[i] == 0;
+    }
     uint8_t* dstatus = nullptr;
     RCK(ws_get_t(w, S_STATUS, L.nb, &dstatus));
-    CK(cudaMemcpyAsync(dstatus, L.status.data(), L.nb, cudaMemcpyHostToDevice, w->stream));
+    CK(cudaMemcpyAsync(dstatus, fst.data(), L.nb, cudaMemcpyHostToDevice, w->stream));
     FillArgs fa;
     fa.field = L.P;
     fa.lx = d[0];
@@ -1607,6 +1651,8 @@ rw_status rw_tree_create(const rw_pyramid* py, const rw_opts* opts_in, rw_tree**
         L.mx.assign(L.nb, 0.0f);
         L.md.assign(L.nb, 0.0f);
         L.status.assign(L.nb, 0);
+        L.filled.assign(L.nb, 0);
+        L.changed.assign(L.nb, 1);
     }
     *out = t;
     return RW_OK;
@@ -1744,6 +1790,48 @@ rw_status rw_trees_argmax(const rw_tree* const* trees, int32_t n_classes, int32_
         CK(counted(launch_argmax(cf, d[0], d[1], sb, lab, prob, w->stream)));
         if (!lab_dev) CK(cudaMemcpyAsync(labels_out + off, lab_st, m, cudaMemcpyDeviceToHost, w->stream));
         if (!prob_dev) CK(cudaMemcpyAsync(prob_out + off, prob_st, m * 4, cudaMemcpyDeviceToHost, w->stream));
+    }
+    return leave(w);
+}
+
+rw_status rw_trees_argmax_changed(const rw_tree* const* trees, int32_t n_classes, uint8_t* labels_out,
+                                  float* prob_out, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!trees || !labels_out || n_classes < 2 || n_classes > RW_MAX_CLASSES)
+        return fail(RW_ERR_INVALID_ARG, "need 2..%d trees and an output", RW_MAX_CLASSES);
+    ClassFields cf{};
+    cf.n = n_classes;
+    const rw_pyramid* py = nullptr;
+    for (int c = 0; c < n_classes; ++c) {
+        if (!trees[c]) return fail(RW_ERR_INVALID_ARG, "tree %d is NULL", c);
+        if (c == 0) py = trees[c]->pyr;
+        else if (trees[c]->pyr != py) return fail(RW_ERR_INVALID_ARG, "trees on different pyramids");
+        if (trees[c]->refined != py->K + 1) return fail(RW_ERR_INVALID_ARG, "tree %d is not fully refined", c);
+        cf.P[c] = trees[c]->L[py->K].P;
+    }
+    uint8_t* lab = is_device_ptr(labels_out) ? labels_out : static_cast<uint8_t*>(pinned_device_alias(labels_out));
+    float* prob = nullptr;
+    if (prob_out) {
+        prob = is_device_ptr(prob_out) ? prob_out : static_cast<float*>(pinned_device_alias(prob_out));
+        if (!prob) return fail(RW_ERR_INVALID_ARG, "prob_out must be device or page-locked host memory");
+    }
+    if (!lab) return fail(RW_ERR_INVALID_ARG, "labels_out must be device or page-locked host memory");
+    const TreeLevel& L0 = trees[0]->L[py->K];
+    std::vector<int64_t> nodes;
+    for (int64_t i = 0; i < L0.nb; ++i) {
+        bool ch = false;
+        for (int c = 0; c < n_classes && !ch; ++c) ch = trees[c]->L[py->K].changed[i] != 0;
+        if (ch) nodes.push_back(i);
+    }
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    if (!nodes.empty()) {
+        int64_t* dn = nullptr;
+        RCK(ws_get_t(w, S_NODES, nodes.size() * sizeof(int64_t), &dn));
+        CK(cudaMemcpyAsync(dn, nodes.data(), nodes.size() * sizeof(int64_t), cudaMemcpyHostToDevice, w->stream));
+        const auto& d = py->dims[py->K];
+        CK(counted(launch_argmax_nodes(cf, d[0], d[1], d[2], py->s, L0.nbx, L0.nby, dn, (int64_t)nodes.size(), lab,
+                                       prob, w->stream)));
     }
     return leave(w);
 }

@@ -255,7 +255,7 @@ struct FillArgs {
     int lx, ly, lz;
     const float* parent;    // level k-1 filled field (nullptr at root)
     int px, py, pz;
-    const uint8_t* status;  // per brick: 0 absent (upsample), 1 solved, 2 reused (both kept in place)
+    const uint8_t* status;  // per brick: 0 = write the upsampled parent, otherwise keep (in place)
     int nbx, nby, nbz, s;
 };
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s);
@@ -264,6 +264,11 @@ struct ClassFields {
     const float* P[8];
     int n;
 };
+// Argmax over the bricks in `nodes` (linear brick indices of a level of
+// lx x ly x lz voxels in bricks of s, nbx x nby bricks per plane), outputs in
+// the level's layout.
+cudaError_t launch_argmax_nodes(const ClassFields& f, int lx, int ly, int lz, int s, int nbx, int nby,
+                                const int64_t* nodes, int64_t n_nodes, uint8_t* labels, float* prob, cudaStream_t st);
 cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t box[6], uint8_t* labels, float* prob,
                           cudaStream_t s);
 cudaError_t launch_read_box(const float* field, int lx, int ly, int lz, const int64_t box[6], float* out,

@@ -160,6 +160,31 @@ def test_incremental_update_parity(rw):
         assert su["bricks_reused"] == ou.stats["bricks_reused"]
 
 
+def test_chained_updates_parity(rw):
+    # three successive incremental passes against the oracle's chained
+    # updates: the level fill rewrites only the absent nodes whose parent
+    # footprint changed, which must still give the oracle's fields
+    ph = P.vessel_tree(n=64, seed=11, n_segments=30)
+    xyz, val = ph["labels_xyz"], ph["labels_value"]
+    cuts = [len(val) - 9, len(val) - 6, len(val) - 3, len(val)]
+    pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-11)
+    tree = rw.Tree(pyr, opts)
+    tree.run(xyz[:cuts[0]], val[:cuts[0]])
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=130.0)
+    ot = hrw.run(levels, xyz[:cuts[0]], val[:cuts[0]], oo)
+    kept = 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        tree.update_seeds(xyz[a:b], val[a:b])
+        ot = hrw.update(ot, xyz[a:b], val[a:b])
+        fl = tree.node_stats(pyr.levels - 1)[0]
+        kept += int(np.count_nonzero((fl & rw.RW_NODE_CHANGED) == 0))
+    assert kept > 0
+    _compare(rw, tree, ot, oo, 8, incremental=True)
+
+
 def test_update_without_labels_keeps_everything(rw):
     ph = P.vessel_tree(n=32, seed=3, n_segments=10)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
@@ -295,6 +320,39 @@ def test_argmax_output_kinds_agree(rw):
             p = p.cpu().numpy() if kind != "numpy" else p
             assert np.array_equal(o, ref_l), (kind, b)
             assert np.array_equal(p, ref_p), (kind, b)
+
+
+def test_argmax_changed_matches_full_argmax(rw):
+    # after each round of updates, relabelling only the changed leaf bricks
+    # (device and page-locked outputs) gives the full argmax bit for bit
+    import torch
+    shape = (64, 64, 64)
+    c = P.multiclass_case(shape, seed=3, n_segments=20, n_blobs=20, n_updates=4)
+    pyr, trees = _class_trees(rw, c, 8, 1e-10, prune=True)
+    lab_d = torch.empty(shape, dtype=torch.uint8, device="cuda")
+    prob_d = torch.empty(shape, dtype=torch.float32, device="cuda")
+    lab_h = torch.empty(shape, dtype=torch.uint8, pin_memory=True)
+    rw.trees_argmax(trees, out=lab_d, prob=prob_d)
+    rw.trees_argmax(trees, out=lab_h)
+    partial = False
+    for xyz, cls in c["updates"]:
+        for k, t in enumerate(trees):
+            t.update_seeds(xyz, np.full(len(xyz), 1.0 if k == cls else 0.0, np.float32),
+                           np.full(len(xyz), cls, np.int32))
+        rw.trees_argmax_changed(trees, lab_d, prob_d)
+        rw.trees_argmax_changed(trees, lab_h)
+        torch.cuda.synchronize()
+        ref_l, ref_p = rw.trees_argmax(trees, prob=np.empty(shape, np.float32))
+        assert np.array_equal(lab_d.cpu().numpy(), ref_l)
+        assert np.array_equal(prob_d.cpu().numpy(), ref_p)
+        assert np.array_equal(lab_h.numpy(), ref_l)
+        ch = np.zeros_like(trees[0].node_stats(pyr.levels - 1)[0], dtype=bool)
+        for t in trees:
+            ch |= (t.node_stats(pyr.levels - 1)[0] & rw.RW_NODE_CHANGED) != 0
+        partial = partial or not ch.all()
+    assert partial
+    with pytest.raises(rw.RWError):
+        rw.trees_argmax_changed(trees, np.empty(shape, np.uint8))
 
 
 def test_poisson_weights_hierarchy_parity(rw):
