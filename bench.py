@@ -110,6 +110,20 @@ def _dist():
     return ws, rank, local
 
 
+def _aggregate(pg, ms, vi, dev):
+    """Whole-job figures over the ranks of process group `pg` (None: one
+    rank): the slowest rank's time and the sum of the voxel-iterations."""
+    if pg is None:
+        return ms, float(vi)
+    import torch
+    t = torch.tensor([ms, float(vi)], device=dev, dtype=torch.float64)
+    tm = t.clone()
+    pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+    ts = t.clone()
+    pg.all_reduce(ts, op=pg.ReduceOp.SUM)
+    return float(tm[0]), float(ts[1])
+
+
 def _cpu_baseline(c, seconds=15.0):
     """The FP64 oracle as it stands on the host cores, on a bounded sample:
     its first M PCG iterations on the same 256^3 system (M sized to ~seconds)."""
@@ -209,15 +223,7 @@ def run(args):
     sweeps = sum(s["sweeps"] for s in stats)
     ms_sweeps = sum(s["ms_sweeps"] for s in stats)
     launches = sum(s["launches"] for s in stats)
-    if pg:
-        t = torch.tensor([ms, float(vi)], device=dev, dtype=torch.float64)
-        tm = t.clone()
-        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
-        ts = t.clone()
-        pg.all_reduce(ts, op=pg.ReduceOp.SUM)
-        ms_all, vi_all = float(tm[0]), float(ts[1])
-    else:
-        ms_all, vi_all = ms, float(vi)
+    ms_all, vi_all = _aggregate(pg, ms, vi, dev)
     value = vi_all / (ms_all / 1e3)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
