@@ -36,10 +36,15 @@ TOL = 1e-8
 # (1 B).  The sweep kernel itself moves 28 B (g and code packed in one word).
 SWEEP_BYTES_PER_VOXEL = 27
 KERNEL_BYTES_PER_VOXEL = 28
-# DRAM bytes of one sweep launch on the 256^3 workload per tile, from an ncu
-# launch list of this benchmark (median over the timed step's sweeps); cleared
-# when the sweep kernel changes until it is captured again
-SWEEP_TRAFFIC_256 = {"s32x22": 466.88e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sweep5
+# launch on the 256^3 workload per tile: median over the launches of each
+# tile (autotuning sweeps included) in one ncu launch list of
+# `bench.py --steps 1 --warmup 3` (profiles/launches_plain256.md); cleared when
+# the sweep kernel changes until it is captured again
+SWEEP_TRAFFIC_256 = {"s32x20": 462.27e6, "s32x20_d3": 458.75e6, "s32x22_d1": 471.94e6, "s32x22": 469.76e6,
+                     "s64x11": 472.25e6, "s64x8_d1": 464.16e6, "s64x8": 455.23e6, "s64x8_d3": 454.41e6}
+
+
 def _workload(n):
     return f"plain random walker, {n}^3 three-ellipsoid phantom (phantoms.plain_ellipsoids, seed 0), beta 130"
 
@@ -269,7 +274,7 @@ def run(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_256.get(tile_name) if N == 256 else None,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, median over "
-                                           "the timed step's k_sweep5 launches of this tile "
+                                           "the k_sweep5 launches of this tile in one launch list "
                                            "(profiles/launches_plain256.md)",
                          "kernel": "k_sweep5 (fused PCG sweep)", "peak_source": src,
                          "algorithmic_bytes_per_launch": alg, "basis": "27 B per free voxel per sweep",
@@ -424,7 +429,8 @@ def run_multiclass(args):
     """Incremental multi-class hierarchy: one tree per class (vessel tree,
     cell blobs, background) on one pyramid, hom-only pruning.  Initial solve
     from three 200-voxel strokes per class; then each step adds one stroke of
-    a random class: all three trees are updated (Sec. IV-E) and the argmax
+    a random class: all three trees are updated together (Sec. IV-E;
+    rw_update_seeds_trees: their bricks share batched solves) and the argmax
     labels of the leaf are recomputed on the leaf bricks that changed in any
     tree (after one full-leaf argmax of the initial solve).  Default volume 1024 x 1024 x 2048
     (x, y, z); --n 2048 runs the full 2048 x 2048 x 4096 workload (three
@@ -461,10 +467,10 @@ def run_multiclass(args):
     t_init = time.perf_counter() - t0
 
     def update(stroke):
+        # the three trees updated together (their bricks share batched solves)
         xyz, cls = stroke
-        st = [t.update_seeds(xyz, np.full(len(xyz), 1.0 if k == cls else 0.0, np.float32),
-                             np.full(len(xyz), cls, np.int32))
-              for k, t in enumerate(trees)]
+        vals = [np.full(len(xyz), 1.0 if k == cls else 0.0, np.float32) for k in range(len(trees))]
+        st = [rw.update_trees(trees, xyz, vals, np.full(len(xyz), cls, np.int32))]
         rw.trees_argmax_changed(trees, labels)  # relabel the leaf bricks that changed
         return st
 

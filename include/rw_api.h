@@ -279,6 +279,17 @@ rw_status rw_refine_level(rw_tree* tree, int32_t level, const rw_labels* labels,
  * their old values and whole old subtree.  Requires a fully refined tree. */
 rw_status rw_update_seeds(rw_tree* tree, const rw_labels* added, rw_stats* stats, void* stream);
 
+/* rw_update_seeds on n_trees trees at once (e.g. one per class of a
+ * multi-class labelling, Sec. III-B): added[i] (array of n_trees entries,
+ * NULL: no new labels) goes to trees[i].  The result of every tree is the one
+ * rw_update_seeds gives; at each level the nodes of all trees are solved in
+ * shared batched launches, so the PCG iterations of the trees run
+ * concurrently.  `stats` (nullable) sums over the trees.  RW_ERR_INVALID_ARG
+ * unless the trees are distinct, fully refined, on one pyramid and have equal
+ * options. */
+rw_status rw_update_seeds_trees(rw_tree* const* trees, int32_t n_trees, const rw_labels* added, rw_stats* stats,
+                                void* stream);
+
 /* Multi-class labelling (Sec. III-B: one random-walker problem per class,
  * class c's labels as 1 and every other class's as 0; the label of a voxel is
  * the class of highest probability).  `trees` holds one refined tree per

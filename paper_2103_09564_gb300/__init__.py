@@ -24,7 +24,7 @@ from ._abi import (RW_CODE_ABSENT, RW_CODE_FREE, RW_CODE_SEED, RW_FP64, RW_MIXED
                    RW_NODE_SIMILAR, RW_NODE_SOLVED, RW_STORE_F32, RW_STORE_UNORM16, LibraryMissing)
 
 __all__ = ["RWError", "Opts", "rw_solve", "rw_solve_noalloc", "rw_solve_adjoint", "rw_build_pyramid", "Pyramid", "Tree",
-           "trees_argmax", "trees_argmax_changed", "load",
+           "trees_argmax", "trees_argmax_changed", "update_trees", "load",
            "release_workspace", "version"]
 
 
@@ -301,6 +301,26 @@ def trees_argmax_changed(trees, out, prob=None):
     _check(load().rw_trees_argmax_changed(arr, len(trees), o.ptr, p.ptr if p else None,
                                           _stream(o, *([p] if p else []))))
     return o.obj, (p.obj if p else None)
+
+
+def update_trees(trees, xyz, values, cls=None):
+    """update_seeds on every tree at once (one tree per class): the label
+    points `xyz` (and classes `cls`) are shared, values[i] are tree i's label
+    values.  The nodes of all trees are solved in shared batches level by
+    level; returns the statistics summed over the trees."""
+    n = len(trees)
+    if len(values) != n:
+        raise ValueError("one array of label values per tree")
+    labs, keep = [], []
+    for v in values:
+        lab, hold = _labels(xyz, v, cls)
+        labs.append(lab)
+        keep.append(hold)
+    arr_t = (ctypes.c_void_p * n)(*[t.h.value for t in trees])
+    arr_l = (_abi.rw_labels * n)(*labs)
+    st = _abi.rw_stats()
+    _check(load().rw_update_seeds_trees(arr_t, n, arr_l, ctypes.byref(st), None))
+    return st.as_dict()
 
 
 def _labels(xyz, value, cls=None):

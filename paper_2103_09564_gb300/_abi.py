@@ -30,7 +30,7 @@ EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspa
            "rw_solve_adjoint",
            "rw_build_pyramid", "rw_build_pyramid_ex", "rw_pyramid_info", "rw_pyramid_read_level", "rw_pyramid_free", "rw_tree_create",
            "rw_refine_level", "rw_update_seeds", "rw_tree_read_level", "rw_tree_node_stats", "rw_tree_free",
-           "rw_trees_argmax", "rw_trees_argmax_changed"]
+           "rw_trees_argmax", "rw_trees_argmax_changed", "rw_update_seeds_trees"]
 
 
 class rw_volume(ctypes.Structure):
@@ -92,6 +92,8 @@ PROTOTYPES = {
     "rw_tree_create": (ctypes.c_int, [_P, ctypes.POINTER(rw_opts), ctypes.POINTER(_P)]),
     "rw_refine_level": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rw_labels), ctypes.POINTER(rw_stats), _P]),
     "rw_update_seeds": (ctypes.c_int, [_P, ctypes.POINTER(rw_labels), ctypes.POINTER(rw_stats), _P]),
+    "rw_update_seeds_trees": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(rw_labels),
+                                             ctypes.POINTER(rw_stats), _P]),
     "rw_tree_read_level": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "rw_tree_node_stats": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "rw_tree_free": (None, [_P]),

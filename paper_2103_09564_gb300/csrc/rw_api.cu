@@ -1252,28 +1252,50 @@ int64_t brick_index(const TreeLevel& L, const std::array<int, 3>& b) {
     return ((int64_t)b[2] * L.nby + b[1]) * L.nbx + b[0];
 }
 
-// Solve every node in `jobs` at level k (batched launches), contract into the
-// level field and evaluate the node predicates.
-rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std::array<int, 3>>& nodes,
-                      const std::vector<LabelVox>& labs, LabelVox* dlab, rw_stats* st) {
-    const rw_pyramid* py = t->pyr;
-    TreeLevel& L = t->L[k];
+// One tree's share of a level solve: its node list and rasterised labels
+// (device copy).
+struct Segment {
+    rw_tree* t;
+    const std::vector<std::array<int, 3>>* nodes;
+    const LabelVox* dlab;
+    int nlab;
+};
+
+// Solve every node of every segment at level k in batched launches: nodes of
+// several trees on one pyramid (equal options) share a batch, each tree
+// gathering from its own parent and old field and receiving its own results.
+// Contract into the level fields and evaluate the node predicates.
+rw_status solve_segments(DevWorkspace* w, int k, const std::vector<Segment>& segs, rw_stats* st) {
+    if (segs.empty()) return RW_OK;
+    const rw_tree* t0 = segs[0].t;
+    const rw_pyramid* py = t0->pyr;
     const auto& d = py->dims[k];
     const int s = py->s;
-    const int se = std::max(s, (int)std::floor((double)t->opts.expand * s));
+    const int se = std::max(s, (int)std::floor((double)t0->opts.expand * s));
     // the root's neighbourhood is the whole root level (dims <= s)
     const int E = (k == 0) ? std::max(d[0], std::max(d[1], d[2])) : se;
-    const int maxb = t->opts.batch_bricks ? t->opts.max_batch : 1;
-    rw_opts o = t->opts;
-    for (size_t off = 0; off < nodes.size(); off += maxb) {
-        const int nb = (int)std::min<size_t>(maxb, nodes.size() - off);
+    const int maxb = t0->opts.batch_bricks ? t0->opts.max_batch : 1;
+    const rw_opts o = t0->opts;
+    std::vector<std::pair<int, int>> ent;  // (segment, node), segments in order
+    for (int g = 0; g < (int)segs.size(); ++g)
+        for (int i = 0; i < (int)segs[g].nodes->size(); ++i) ent.push_back({g, i});
+    for (size_t off = 0; off < ent.size(); off += maxb) {
+        const int nb = (int)std::min<size_t>(maxb, ent.size() - off);
         std::vector<BrickJob> jobs(nb);
         std::vector<int> ext(3 * nb);
         for (int i = 0; i < nb; ++i) {
-            jobs[i] = make_job(t, k, nodes[off + i]);
+            const auto& e = ent[off + i];
+            jobs[i] = make_job(segs[e.first].t, k, (*segs[e.first].nodes)[e.second]);
             ext[3 * i] = jobs[i].ex;
             ext[3 * i + 1] = jobs[i].ey;
             ext[3 * i + 2] = jobs[i].ez;
+        }
+        // runs of one segment within the batch: {segment, first, end}
+        std::vector<std::array<int, 3>> runs;
+        for (int i = 0; i < nb; ++i) {
+            const int g = ent[off + i].first;
+            if (runs.empty() || runs.back()[0] != g) runs.push_back({g, i, i});
+            runs.back()[2] = i + 1;
         }
         BrickJob* djobs = nullptr;
         int *dext = nullptr, *dflags = nullptr;
@@ -1295,24 +1317,34 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
         bx.nbox = nb;
         bx.nx = bx.ny = bx.nz = E;
         bx.ext = dext;
-        GatherArgs ga;
-        ga.bx = bx;
-        ga.jobs = djobs;
-        ga.gq = (k == py->K) ? py->leaf : nullptr;
-        ga.gf = (k == py->K) ? nullptr : py->lv[k];
-        ga.lx = d[0];
-        ga.ly = d[1];
-        ga.lz = d[2];
-        ga.parent = k > 0 ? t->L[k - 1].P : nullptr;
-        ga.px = k > 0 ? py->dims[k - 1][0] : 1;
-        ga.py = k > 0 ? py->dims[k - 1][1] : 1;
-        ga.pz = k > 0 ? py->dims[k - 1][2] : 1;
-        ga.init = t->update ? L.P : nullptr;  // warm start: the previous pass's field (in place)
-        ga.g_out = pg;
-        ga.code_out = pcode;
-        ga.x_out = px;
-        CK(counted(launch_gather(ga, w->stream)));
-        CK(counted(launch_apply_labels(bx, djobs, dlab, (int)labs.size(), pcode, px, dflags, w->stream)));
+        auto sub = [&](const std::array<int, 3>& r) {
+            Boxes b = bx;
+            b.nbox = r[2] - r[1];
+            b.ext = dext + 3 * r[1];
+            return b;
+        };
+        for (const auto& r : runs) {
+            const rw_tree* t = segs[r[0]].t;
+            GatherArgs ga;
+            ga.bx = sub(r);
+            ga.jobs = djobs + r[1];
+            ga.gq = (k == py->K) ? py->leaf : nullptr;
+            ga.gf = (k == py->K) ? nullptr : py->lv[k];
+            ga.lx = d[0];
+            ga.ly = d[1];
+            ga.lz = d[2];
+            ga.parent = k > 0 ? t->L[k - 1].P : nullptr;
+            ga.px = k > 0 ? py->dims[k - 1][0] : 1;
+            ga.py = k > 0 ? py->dims[k - 1][1] : 1;
+            ga.pz = k > 0 ? py->dims[k - 1][2] : 1;
+            ga.init = t->update ? t->L[k].P : nullptr;  // warm start: the previous pass's field (in place)
+            ga.g_out = pg + r[1] * pv;
+            ga.code_out = pcode + r[1] * pv;
+            ga.x_out = px + r[1] * pv;
+            CK(counted(launch_gather(ga, w->stream)));
+            CK(counted(launch_apply_labels(ga.bx, ga.jobs, segs[r[0]].dlab, segs[r[0]].nlab, ga.code_out, ga.x_out,
+                                           dflags + r[1], w->stream)));
+        }
         SolveProblem P;
         P.bx = bx;
         P.g = pg;
@@ -1327,28 +1359,44 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
         RCK(solve_boxes(w, P, o, &R));
         int bad = 0, nos = 0;
         stats_from(R, o, st, &bad, &nos);
-        ContractArgs ca;
-        ca.bx = bx;
-        ca.jobs = djobs;
-        ca.s = s;
-        ca.x = px;
-        ca.field = L.P;
         // an incremental pass updates the field in place: statistics first
         // (against the old values), then the bricks that are not similar
-        ca.old = t->update ? L.P : nullptr;
-        ca.stats_only = t->update ? 1 : 0;
-        ca.lx = d[0];
-        ca.ly = d[1];
-        ca.lz = d[2];
-        ca.stats = dstats;
-        CK(counted(launch_contract(ca, w->stream)));
+        auto contract = [&](const std::array<int, 3>& r, bool write_pass) -> cudaError_t {
+            rw_tree* t = segs[r[0]].t;
+            ContractArgs ca;
+            ca.bx = sub(r);
+            ca.jobs = djobs + r[1];
+            ca.s = s;
+            ca.x = px + r[1] * pv;
+            ca.field = t->L[k].P;
+            ca.lx = d[0];
+            ca.ly = d[1];
+            ca.lz = d[2];
+            if (write_pass) {
+                ca.old = nullptr;
+                ca.stats_only = 0;
+                ca.stats = nullptr;
+                ca.skip = dflags + r[1];
+            } else {
+                ca.old = t->update ? t->L[k].P : nullptr;
+                ca.stats_only = t->update ? 1 : 0;
+                ca.stats = dstats + 3 * r[1];
+            }
+            return launch_contract(ca, w->stream);
+        };
+        for (const auto& r : runs) CK(counted(contract(r, false)));
         std::vector<float> hst(3 * nb);
         std::vector<int> hfl(nb);
         CK(cudaMemcpyAsync(hst.data(), dstats, nb * 3 * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaMemcpyAsync(hfl.data(), dflags, nb * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaStreamSynchronize(w->stream));
+        bool any_update = false;
         for (int i = 0; i < nb; ++i) {
-            const int64_t bi = brick_index(L, nodes[off + i]);
+            const auto& e = ent[off + i];
+            rw_tree* t = segs[e.first].t;
+            TreeLevel& L = t->L[k];
+            any_update = any_update || t->update;
+            const int64_t bi = brick_index(L, (*segs[e.first].nodes)[e.second]);
             const float mn = hst[3 * i], mx = hst[3 * i + 1], md = hst[3 * i + 2];
             int f = RW_NODE_SOLVED | (hfl[i] & (RW_NODE_CFL | RW_NODE_CFL_ADDED));
             if (R.sc[i].nseed == 0) f |= RW_NODE_NO_SEEDS;
@@ -1371,13 +1419,10 @@ rw_status solve_nodes(DevWorkspace* w, rw_tree* t, int k, const std::vector<std:
                 if (cfl) st->bricks_conflict += 1;
             }
         }
-        if (t->update) {
+        if (any_update) {
             CK(cudaMemcpyAsync(dflags, hfl.data(), nb * sizeof(int), cudaMemcpyHostToDevice, w->stream));
-            ca.old = nullptr;
-            ca.stats_only = 0;
-            ca.stats = nullptr;
-            ca.skip = dflags;
-            CK(counted(launch_contract(ca, w->stream)));
+            for (const auto& r : runs)
+                if (segs[r[0]].t->update) CK(counted(contract(r, true)));
         }
     }
     return RW_OK;
@@ -1403,30 +1448,40 @@ bool parent_changed(const rw_tree* t, int k, const std::array<int, 3>& b) {
     return false;
 }
 
-rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
-    const rw_pyramid* py = t->pyr;
-    TreeLevel& L = t->L[k];
-    const auto& d = py->dims[k];
+// The work of one tree at one level: the nodes to solve, those reused from
+// the previous pass, and the level's rasterised labels.
+struct LevelWork {
     std::vector<std::array<int, 3>> nodes, reuse;
+    std::vector<LabelVox> labs;
+};
+
+void level_begin(rw_tree* t, int k, LevelWork* lw) {
+    TreeLevel& L = t->L[k];
+    lw->nodes.clear();
+    lw->reuse.clear();
     if (k == 0) {
-        nodes.push_back({0, 0, 0});
+        lw->nodes.push_back({0, 0, 0});
     } else {
-        nodes = t->resolve;
-        reuse = t->reused;
+        lw->nodes = t->resolve;
+        lw->reuse = t->reused;
     }
     std::fill(L.flags.begin(), L.flags.end(), 0);
     std::fill(L.mn.begin(), L.mn.end(), 0.0f);
     std::fill(L.mx.begin(), L.mx.end(), 0.0f);
     std::fill(L.md.begin(), L.md.end(), 0.0f);
     std::fill(L.status.begin(), L.status.end(), 0);
-    std::vector<LabelVox> labs;
-    rasterize(t, k, &labs);
-    LabelVox* dlab = nullptr;
-    RCK(ws_get_t(w, S_LAB, std::max<size_t>(1, labs.size()) * sizeof(LabelVox), &dlab));
-    if (!labs.empty())
-        CK(cudaMemcpyAsync(dlab, labs.data(), labs.size() * sizeof(LabelVox), cudaMemcpyHostToDevice, w->stream));
-    if (st) st->bricks_active += (int64_t)nodes.size();
-    RCK(solve_nodes(w, t, k, nodes, labs, dlab, st));
+    lw->labs.clear();
+    rasterize(t, k, &lw->labs);
+}
+
+// After the level's solve: node status, change tracking, the level fill and
+// the next level's node lists.
+rw_status level_end(rw_tree* t, int k, const LevelWork& lw, rw_stats* st, DevWorkspace* w) {
+    const rw_pyramid* py = t->pyr;
+    TreeLevel& L = t->L[k];
+    const auto& d = py->dims[k];
+    const auto& nodes = lw.nodes;
+    const auto& reuse = lw.reuse;
     std::vector<std::array<int, 3>> nres, nreu;
     for (const auto& b : nodes) {
         const int64_t bi = brick_index(L, b);
@@ -1502,11 +1557,102 @@ rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) {
     return RW_OK;
 }
 
-rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
+// Level k of every tree in `trees` (one pyramid, equal options): their
+// nodes are solved together, batch by batch.
+rw_status process_levels(rw_tree* const* trees, int n, int k, rw_stats* st, DevWorkspace* w) {
+    std::vector<LevelWork> lw(n);
+    size_t nl = 0;
+    for (int i = 0; i < n; ++i) {
+        level_begin(trees[i], k, &lw[i]);
+        nl += lw[i].labs.size();
+        if (st) st->bricks_active += (int64_t)lw[i].nodes.size();
+    }
+    LabelVox* dlab = nullptr;
+    RCK(ws_get_t(w, S_LAB, std::max<size_t>(1, nl) * sizeof(LabelVox), &dlab));
+    std::vector<Segment> segs;
+    size_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t m = lw[i].labs.size();
+        if (m)
+            CK(cudaMemcpyAsync(dlab + o, lw[i].labs.data(), m * sizeof(LabelVox), cudaMemcpyHostToDevice,
+                               w->stream));
+        segs.push_back({trees[i], &lw[i].nodes, dlab + o, (int)m});
+        o += m;
+    }
+    RCK(solve_segments(w, k, segs, st));
+    for (int i = 0; i < n; ++i) RCK(level_end(trees[i], k, lw[i], st, w));
+    return RW_OK;
+}
+
+rw_status process_level(rw_tree* t, int k, rw_stats* st, DevWorkspace* w) { return process_levels(&t, 1, k, st, w); }
+
+bool same_solver_opts(const rw_opts& a, const rw_opts& b) {
+    return a.beta == b.beta && a.w_min == b.w_min && a.tol == b.tol && a.max_iter == b.max_iter &&
+           a.precision == b.precision && a.refine_rounds == b.refine_rounds && a.brick_size == b.brick_size &&
+           a.expand == b.expand && a.t_hom == b.t_hom && a.t_bin == b.t_bin && a.t_inc == b.t_inc &&
+           a.prune_hom == b.prune_hom && a.prune_dt == b.prune_dt && a.iters_per_graph == b.iters_per_graph &&
+           a.tile == b.tile && a.batch_bricks == b.batch_bricks && a.max_batch == b.max_batch && a.weight == b.weight;
+}
+
+rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added);
+rw_status check_labels(const rw_labels* lab);
+
+// Incremental pass (Sec. IV-E) over n trees on one pyramid with equal
+// options; added[i] (nullable) holds tree i's new labels.  Level by level the
+// nodes of all trees are solved together.
+rw_status update_trees(rw_tree* const* trees, int n, const rw_labels* added, rw_stats* stats, void* stream) {
+    g_launches = 0;
+    const double t0 = now_ms();
+    for (int i = 0; i < n; ++i) {
+        rw_tree* t = trees[i];
+        if (!t) return fail(RW_ERR_INVALID_ARG, "tree %d is NULL", i);
+        if (t->refined != t->pyr->K + 1) return fail(RW_ERR_INVALID_ARG, "tree %d is not fully refined", i);
+        if (t->pyr != trees[0]->pyr) return fail(RW_ERR_INVALID_ARG, "trees on different pyramids");
+        if (!same_solver_opts(t->opts, trees[0]->opts)) return fail(RW_ERR_INVALID_ARG, "trees with different options");
+        for (int j = 0; j < i; ++j)
+            if (trees[j] == t) return fail(RW_ERR_INVALID_ARG, "tree %d given twice", i);
+        RCK(check_labels(added ? &added[i] : nullptr));
+    }
+    if (stats) memset(stats, 0, sizeof(*stats));
+    for (int i = 0; i < n; ++i) {
+        for (auto& a : trees[i]->lab_added) a = 0;
+        RCK(copy_labels(trees[i], added ? &added[i] : nullptr, 1));
+    }
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    for (int i = 0; i < n; ++i) {
+        trees[i]->update = 1;
+        trees[i]->resolve.clear();
+        trees[i]->reused.clear();
+        trees[i]->refined = 0;
+    }
+    for (int k = 0; k <= trees[0]->pyr->K; ++k) {
+        RCK(process_levels(trees, n, k, stats, w));
+        for (int i = 0; i < n; ++i) trees[i]->refined = k + 1;
+    }
+    for (int i = 0; i < n; ++i) {
+        trees[i]->update = 0;
+        for (auto& a : trees[i]->lab_added) a = 0;
+    }
+    RCK(leave(w));
+    if (stats) {
+        stats->ms = now_ms() - t0;
+        stats->launches = g_launches;
+    }
+    return RW_OK;
+}
+
+rw_status check_labels(const rw_labels* lab) {
     if (!lab || lab->n <= 0) return RW_OK;
     if (!lab->xyz || !lab->value) return fail(RW_ERR_INVALID_ARG, "labels with NULL arrays");
     if (is_device_ptr(lab->xyz) || is_device_ptr(lab->value) || (lab->cls && is_device_ptr(lab->cls)))
         return fail(RW_ERR_INVALID_ARG, "labels must be in host memory");
+    return RW_OK;
+}
+
+rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
+    RCK(check_labels(lab));
+    if (!lab || lab->n <= 0) return RW_OK;
     for (int64_t i = 0; i < lab->n; ++i) {
         t->lab_xyz.push_back(lab->xyz[3 * i]);
         t->lab_xyz.push_back(lab->xyz[3 * i + 1]);
@@ -1693,32 +1839,15 @@ rw_status rw_refine_level(rw_tree* t, int32_t level, const rw_labels* labels, rw
 
 rw_status rw_update_seeds(rw_tree* t, const rw_labels* added, rw_stats* stats, void* stream) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
-    g_launches = 0;
-    const double t0 = now_ms();
     if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
-    if (t->refined != t->pyr->K + 1) return fail(RW_ERR_INVALID_ARG, "tree is not fully refined");
-    if (stats) memset(stats, 0, sizeof(*stats));
-    for (auto& a : t->lab_added) a = 0;
-    RCK(copy_labels(t, added, 1));
-    DevWorkspace* w = nullptr;
-    RCK(enter(&w, stream));
-    t->update = 1;
-    t->resolve.clear();
-    t->reused.clear();
-    t->refined = 0;
-    for (int k = 0; k <= t->pyr->K; ++k) {
-        rw_status st = process_level(t, k, stats, w);
-        if (st != RW_OK) return st;
-        t->refined = k + 1;
-    }
-    t->update = 0;
-    for (auto& a : t->lab_added) a = 0;
-    RCK(leave(w));
-    if (stats) {
-        stats->ms = now_ms() - t0;
-        stats->launches = g_launches;
-    }
-    return RW_OK;
+    return update_trees(&t, 1, added, stats, stream);
+}
+
+rw_status rw_update_seeds_trees(rw_tree* const* trees, int32_t n_trees, const rw_labels* added, rw_stats* stats,
+                                void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!trees || n_trees < 1) return fail(RW_ERR_INVALID_ARG, "need at least one tree");
+    return update_trees(trees, n_trees, added, stats, stream);
 }
 
 rw_status rw_tree_read_level(const rw_tree* t, int32_t level, const int64_t box[6], float* out, void* stream) {

@@ -355,6 +355,53 @@ def test_argmax_changed_matches_full_argmax(rw):
         rw.trees_argmax_changed(trees, np.empty(shape, np.uint8))
 
 
+def test_update_trees_matches_oracle_and_sequential_updates(rw):
+    # the class trees updated together (their bricks share batched launches)
+    # give every tree the oracle's incremental result, and the same decisions
+    # and fields as updating the trees one by one
+    c = P.multiclass_case((64, 64, 64), seed=5, n_segments=20, n_blobs=20, n_updates=2)
+    pyr = rw.rw_build_pyramid(c["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-11, prune_hom=1, prune_dt=0)
+    joint = [rw.Tree(pyr, opts) for _ in range(3)]
+    seq = [rw.Tree(pyr, opts) for _ in range(3)]
+    q = O.quantize(c["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), 8)
+    oo = hrw.Opts(brick_size=8, beta=130.0, prune_hom=True, prune_dt=False)
+    ot = []
+    for k in range(3):
+        lab = P.class_labels(c["strokes"], k)
+        joint[k].run(*lab)
+        seq[k].run(*lab)
+        ot.append(hrw.run(levels, lab[0], lab[1], oo, labels_cls=lab[2]))
+    for xyz, cu in c["updates"]:
+        vals = [np.full(len(xyz), 1.0 if k == cu else 0.0, np.float32) for k in range(3)]
+        cl = np.full(len(xyz), cu, np.int32)
+        st = rw.update_trees(joint, xyz, vals, cl)
+        ss = [seq[k].update_seeds(xyz, vals[k], cl) for k in range(3)]
+        assert st["bricks_solved"] == sum(x["bricks_solved"] for x in ss)
+        assert st["bricks_reused"] == sum(x["bricks_reused"] for x in ss)
+        ot = [hrw.update(ot[k], xyz, vals[k], add_cls=cl) for k in range(3)]
+    K = pyr.levels - 1
+    seeds = np.zeros(q.shape, bool)
+    for xyz, _ in list(c["strokes"]) + list(c["updates"]):
+        v = np.floor(xyz).astype(int)
+        seeds[v[:, 2], v[:, 1], v[:, 0]] = True
+    det = determined_mask(O.leaf_level(q), 130.0, seeds=seeds)
+    assert det.mean() > 0.99
+    for k in range(3):
+        _compare(rw, joint[k], ot[k], oo, 8, incremental=True)
+        for lv in range(K + 1):
+            assert np.array_equal(joint[k].node_stats(lv)[0], seq[k].node_stats(lv)[0]), (k, lv)
+        a, b = joint[k].read_level(K), seq[k].read_level(K)
+        assert np.max(np.abs(a - b)[det]) <= TOL
+    with pytest.raises(rw.RWError):
+        rw.update_trees([joint[0], joint[0]], c["updates"][0][0], [vals[0], vals[0]])
+    other = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-10, prune_hom=1, prune_dt=0))
+    other.run(*P.class_labels(c["strokes"], 0))
+    with pytest.raises(rw.RWError):
+        rw.update_trees([joint[0], other], c["updates"][0][0], [vals[0], vals[1]])
+
+
 def test_poisson_weights_hierarchy_parity(rw):
     S = 255.0
     c = P.poisson_ball(n=64, seed=5)
