@@ -434,8 +434,8 @@ def run_multiclass(args):
     labels of the leaf are recomputed on the leaf bricks that changed in any
     tree (after one full-leaf argmax of the initial solve).  Default volume 1024 x 1024 x 2048
     (x, y, z); --n 2048 runs the full 2048 x 2048 x 4096 workload (three
-    trees of 78.5 GB, the pyramid 44 GB: batches of --max-batch bricks and
-    the leaf labels in pinned host memory keep it within HBM)."""
+    trees of 78.5 GB and 17 GB of labels in HBM, the pyramid's 34 GB leaf in
+    host memory, batches of --max-batch bricks)."""
     import torch
     import paper_2103_09564_gb300 as rw
     import phantoms as P
@@ -447,17 +447,18 @@ def run_multiclass(args):
     c = P.multiclass_case(shape, seed=0, n_segments=200, n_blobs=400, n_updates=n_up, device=dev)
     t_phantom = time.perf_counter() - t0
     torch.cuda.empty_cache()  # the library allocates outside torch's cache
-    pyr = rw.rw_build_pyramid(c["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    nvox = shape[0] * shape[1] * shape[2]
+    # full size: the leaf intensities (read only by the leaf-level gathers) in
+    # host memory, so that the trees and the labels fit in HBM
+    leaf_host = args.leaf_host or nvox > (1 << 32)
+    pyr = rw.rw_build_pyramid(c["volume"], s, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=leaf_host)
     del c["volume"]
     torch.cuda.empty_cache()
     kw = {"max_batch": args.max_batch} if args.max_batch else {}
-    opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol, prune_hom=1, prune_dt=0, **kw)
+    opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol, prune_hom=1, prune_dt=0, leaf_field="hbm", **kw)
     trees = [rw.Tree(pyr, opts) for _ in range(3)]
+    labels = torch.empty(shape, dtype=torch.uint8, device=dev)
     free_after_trees = torch.cuda.mem_get_info(dev)[0] / 1e9
-    nvox = shape[0] * shape[1] * shape[2]
-    labels_host = nvox > (1 << 32)
-    labels = (torch.empty(shape, dtype=torch.uint8, pin_memory=True) if labels_host
-              else torch.empty(shape, dtype=torch.uint8, device=dev))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k, t in enumerate(trees):
@@ -492,7 +493,7 @@ def run_multiclass(args):
     # sampled check of the leaf labels kept up to date brick by brick: the
     # argmax of the three trees' own fields on 8 boxes of 32^3
     rs = np.random.default_rng(0)
-    lab_np = labels.cpu().numpy() if not labels_host else labels.numpy()
+    lab_np = labels.cpu().numpy()
     n_chk = n_bad = 0
     for _ in range(8):
         z0, y0, x0 = (int(rs.integers(0, d - 32 + 1)) for d in shape)
@@ -518,7 +519,7 @@ def run_multiclass(args):
                                    f"{shape[0]} uint16 (phantoms.multiclass_case, seed 0), brick {s}, hom pruning, "
                                    f"tol {args.tol}; one step = one added stroke: 3 tree updates + argmax "
                                    f"over the changed leaf bricks"
-                                   + (" (leaf labels to pinned host memory)" if labels_host else "")
+                                   + (" (leaf intensities in host memory; trees and labels in HBM)" if leaf_host else "")
                                    + (f", batches of {args.max_batch} bricks" if args.max_batch else ""),
                        "update_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                              "max": float(np.max(lat))},

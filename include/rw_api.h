@@ -126,6 +126,8 @@ typedef struct rw_opts {
     int32_t batch_bricks;  /* 1: one batched launch per level (default); 0: bricks one by one */
     int32_t max_batch;     /* bricks per batched launch, default 8192 */
     int32_t weight;        /* rw_weight: edge weight function, default RW_WEIGHT_GAUSSIAN */
+    int32_t leaf_field;    /* rw_leaf_field: where a tree keeps its leaf-level field, default
+                              RW_LEAF_AS_PYRAMID (placement only: results are identical) */
 } rw_opts;
 
 /* Edge weight functions (Sec. III-B / III-C).
@@ -241,9 +243,14 @@ rw_status rw_solve_adjoint(const rw_volume* vol, const rw_seed_mask* seeds, cons
  * with ceil-halved dims, until every dim is <= brick_size (the root). */
 rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid** out, void* stream);
 
+/* Placement of a tree's leaf-level field (rw_opts.leaf_field):
+ * RW_LEAF_AS_PYRAMID: host memory when the pyramid's leaf is (RW_PYR_LEAF_HOST),
+ * else HBM; RW_LEAF_HBM / RW_LEAF_HOST: HBM / pinned, mapped host memory. */
+typedef enum rw_leaf_field { RW_LEAF_AS_PYRAMID = 0, RW_LEAF_HBM = 1, RW_LEAF_HOST = 2 } rw_leaf_field;
+
 /* rw_build_pyramid with placement flags.  RW_PYR_LEAF_HOST: the leaf level
- * (its unorm16 intensities here, and the leaf probability fields of every
- * tree created on this pyramid) lives in pinned, mapped host memory instead
+ * (its unorm16 intensities here, and by default the leaf probability fields
+ * of the trees created on this pyramid) lives in pinned, mapped host memory instead
  * of HBM; the GPU reads and writes it in place over the host link.  This is
  * the out-of-core mode of Sec. III (volumes whose leaf does not fit in GPU
  * memory): only the coarser levels (about 1/7 of the leaf) and the brick

@@ -55,7 +55,8 @@ def _check(st: int, allow=()):
 def Opts(**kw) -> _abi.rw_opts:
     """rw_opts with the library defaults, overridden by keyword (precision may
     be 'mixed'/'fp64', tile a name such as '40x8', weight 'gaussian'/'poisson'
-    -- for 'poisson', beta is the count that g = 1 stands for)."""
+    -- for 'poisson', beta is the count that g = 1 stands for --, leaf_field
+    'pyramid'/'hbm'/'host')."""
     o = _abi.rw_opts()
     load().rw_opts_default(ctypes.byref(o))
     for k, v in kw.items():
@@ -65,6 +66,8 @@ def Opts(**kw) -> _abi.rw_opts:
             v = _abi.RW_TILE[v]
         if k == "weight" and isinstance(v, str):
             v = {"gaussian": 0, "poisson": 1}[v]
+        if k == "leaf_field" and isinstance(v, str):
+            v = {"pyramid": _abi.RW_LEAF_AS_PYRAMID, "hbm": _abi.RW_LEAF_HBM, "host": _abi.RW_LEAF_HOST}[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(o, k, v)

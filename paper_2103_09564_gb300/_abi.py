@@ -14,6 +14,7 @@ STATUS_NAMES = ["RW_OK", "RW_ERR_INVALID_ARG", "RW_ERR_NO_SEEDS", "RW_ERR_NOT_CO
 RW_U16, RW_F32 = 0, 1
 RW_STORE_UNORM16, RW_STORE_F32 = 0, 1
 RW_MIXED, RW_FP64 = 0, 1
+RW_LEAF_AS_PYRAMID, RW_LEAF_HBM, RW_LEAF_HOST = 0, 1, 2
 RW_CODE_FREE, RW_CODE_SEED, RW_CODE_ABSENT = 0, 1, 2
 RW_NODE_SOLVED, RW_NODE_PRUNABLE, RW_NODE_HOM, RW_NODE_DT, RW_NODE_CFL, RW_NODE_SIMILAR, RW_NODE_REUSED, \
     RW_NODE_CFL_ADDED, RW_NODE_NO_SEEDS, RW_NODE_CHANGED = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
@@ -53,7 +54,8 @@ class rw_opts(ctypes.Structure):
                 ("brick_size", ctypes.c_int32), ("expand", ctypes.c_float), ("t_hom", ctypes.c_float),
                 ("t_bin", ctypes.c_float), ("t_inc", ctypes.c_float), ("prune_hom", ctypes.c_int32),
                 ("prune_dt", ctypes.c_int32), ("iters_per_graph", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("batch_bricks", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("weight", ctypes.c_int32)]
+                ("batch_bricks", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("weight", ctypes.c_int32),
+                ("leaf_field", ctypes.c_int32)]
 
 
 class rw_stats(ctypes.Structure):

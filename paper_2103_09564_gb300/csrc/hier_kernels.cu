@@ -275,30 +275,38 @@ cudaError_t launch_contract(const ContractArgs& a, cudaStream_t s) {
 // nearest transitive parent's values, Sec. IV-D1).  The field is updated in
 // place: solved nodes were written by k_contract, reused nodes keep the
 // values of the previous pass.
-// One thread per 4 consecutive voxels of a row (grid: x quads and rows in
-// x / y, planes in z).  Children 4q .. 4q+3 of a row read parent columns
-// 2q-1 .. 2q+2 (clamped); each column is interpolated in y, then z, and the
+// One thread per 8 consecutive voxels of a row (grid: x octets and rows in
+// x / y, planes in z).  Children 8q .. 8q+7 of a row read parent columns
+// 4q-1 .. 4q+4 (clamped); each column is interpolated in y, then z, and the
 // children combine two columns with weights 1/4, 3/4 (the taps of
-// upsample_at, applied axis by axis).
+// upsample_at, applied axis by axis).  Brick indices by shifts when s is a
+// power of two.
 __global__ void k_fill(const FillArgs a) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    const int X0 = 4 * q;
+    const int X0 = 8 * q;
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int Z = blockIdx.z;
     if (X0 >= a.lx || Y >= a.ly) return;
-    const int64_t row = ((int64_t)Z * a.ly + Y) * a.lx;
-    const uint8_t* strow = a.status + (int64_t)((Z / a.s) * a.nby + (Y / a.s)) * a.nbx;
-    bool wr[4];
-    if ((a.s & 3) == 0) {  // the quad lies in one brick
-        const bool w = strow[X0 / a.s] == 0;
+    const bool pow2 = (a.s & (a.s - 1)) == 0;
+    const int sh = __ffs(a.s) - 1;
+    const int bz = pow2 ? Z >> sh : Z / a.s, by = pow2 ? Y >> sh : Y / a.s;
+    const uint8_t* strow = a.status + (int64_t)(bz * a.nby + by) * a.nbx;
+    bool wr[8];
+    if ((a.s & 7) == 0) {  // the octet lies in one brick
+        const bool w = strow[pow2 ? X0 >> sh : X0 / a.s] == 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) wr[k] = w && X0 + k < a.lx;
+        for (int k = 0; k < 8; ++k) wr[k] = w && X0 + k < a.lx;
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) wr[k] = X0 + k < a.lx && strow[(X0 + k) / a.s] == 0;
+        for (int k = 0; k < 8; ++k) wr[k] = X0 + k < a.lx && strow[(X0 + k) / a.s] == 0;
     }
-    if (!(wr[0] || wr[1] || wr[2] || wr[3])) return;
-    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) any = any || wr[k];
+    if (!any) return;
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.0f;
     if (a.parent) {
         int ya, yb, za, zb;
         float wya, wyb, wza, wzb;
@@ -309,33 +317,38 @@ __global__ void k_fill(const FillArgs a) {
         const float* Pab = a.parent + za * sz + yb * sy;
         const float* Pba = a.parent + zb * sz + ya * sy;
         const float* Pbb = a.parent + zb * sz + yb * sy;
-        float c[4];
+        float c[6];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = min(max(2 * q - 1 + k, 0), a.px - 1);
+        for (int k = 0; k < 6; ++k) {
+            const int j = min(max(4 * q - 1 + k, 0), a.px - 1);
             const float ca = fmaf(wya, Paa[j], wyb * Pab[j]);  // z = za
             const float cb = fmaf(wya, Pba[j], wyb * Pbb[j]);  // z = zb
             c[k] = fmaf(wza, ca, wzb * cb);
         }
-        v[0] = fmaf(0.25f, c[0], 0.75f * c[1]);
-        v[1] = fmaf(0.75f, c[1], 0.25f * c[2]);
-        v[2] = fmaf(0.25f, c[1], 0.75f * c[2]);
-        v[3] = fmaf(0.75f, c[2], 0.25f * c[3]);
-    }
-    float* out = a.field + row + X0;
-    if (wr[0] && wr[1] && wr[2] && wr[3] && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0)) {
-        *reinterpret_cast<float4*>(out) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (wr[k]) out[k] = v[k];
+        for (int m = 0; m < 8; m += 2) {
+            const int h = m >> 1;
+            v[m] = fmaf(0.25f, c[h], 0.75f * c[h + 1]);
+            v[m + 1] = fmaf(0.75f, c[h + 1], 0.25f * c[h + 2]);
+        }
+    }
+    float* out = a.field + ((int64_t)Z * a.ly + Y) * a.lx + X0;
+#pragma unroll
+    for (int h = 0; h < 8; h += 4) {
+        if (wr[h] && wr[h + 1] && wr[h + 2] && wr[h + 3] && ((reinterpret_cast<uintptr_t>(out + h) & 15u) == 0)) {
+            *reinterpret_cast<float4*>(out + h) = make_float4(v[h], v[h + 1], v[h + 2], v[h + 3]);
+        } else {
+#pragma unroll
+            for (int k = h; k < h + 4; ++k)
+                if (wr[k]) out[k] = v[k];
+        }
     }
 }
 
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
     if ((int64_t)a.lx * a.ly * a.lz == 0) return cudaSuccess;
     const dim3 blk(32, 8, 1);
-    const dim3 grid((unsigned)((a.lx + 127) / 128), (unsigned)((a.ly + 7) / 8), (unsigned)a.lz);
+    const dim3 grid((unsigned)((a.lx + 255) / 256), (unsigned)((a.ly + 7) / 8), (unsigned)a.lz);
     k_fill<<<grid, blk, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -349,37 +362,69 @@ __global__ void k_read_box(const float* field, int lx, int ly, int x0, int y0, i
     out[k] = field[((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x)];
 }
 
-// Multi-class labels: argmax over the class fields of one level (ties: the
-// lowest class index) on a box of the level.  One thread per 4 consecutive
-// outputs (x fastest), stored as one 32-bit word (labels) and one 128-bit
-// word (probabilities) where aligned: the outputs may be page-locked host
-// memory, written across the host link.
-__global__ void k_argmax(const ClassFields f, int lx, int ly, int x0, int y0, int z0, int bx, int by, int bz,
-                         uint8_t* labels, float* prob) {
-    const int64_t n = (int64_t)bx * by * bz;
-    const int64_t k0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-    if (k0 >= n) return;
-    int x, y, z;
-    vox_xyz(k0, bx, by, n, &x, &y, &z);
-    uint32_t lw = 0;
-    float pv[4] = {0.f, 0.f, 0.f, 0.f};
-    const int m = n - k0 < 4 ? (int)(n - k0) : 4;
-    for (int j = 0; j < m; ++j) {
-        const int64_t i = ((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x);
-        int best = 0;
-        float pb = f.P[0][i];
+// Argmax over the class fields (ties: the lowest class index) of m <= 4
+// consecutive voxels starting at level index i0; one 128-bit load per class
+// when the four voxels are aligned.
+__device__ __forceinline__ void argmax4(const ClassFields& f, int64_t i0, int m, uint32_t* lw, float* pv) {
+    *lw = 0;
+    if (m == 4 && (i0 & 3) == 0) {
+        float4 b = *reinterpret_cast<const float4*>(f.P[0] + i0);
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
         for (int c = 1; c < f.n; ++c) {
-            const float v = f.P[c][i];
+            const float4 v = *reinterpret_cast<const float4*>(f.P[c] + i0);
+            if (v.x > b.x) b.x = v.x, c0 = c;
+            if (v.y > b.y) b.y = v.y, c1 = c;
+            if (v.z > b.z) b.z = v.z, c2 = c;
+            if (v.w > b.w) b.w = v.w, c3 = c;
+        }
+        *lw = (uint32_t)c0 | ((uint32_t)c1 << 8) | ((uint32_t)c2 << 16) | ((uint32_t)c3 << 24);
+        pv[0] = b.x, pv[1] = b.y, pv[2] = b.z, pv[3] = b.w;
+        return;
+    }
+    for (int j = 0; j < m; ++j) {
+        int best = 0;
+        float pb = f.P[0][i0 + j];
+        for (int c = 1; c < f.n; ++c) {
+            const float v = f.P[c][i0 + j];
             if (v > pb) {
                 pb = v;
                 best = c;
             }
         }
-        lw |= (uint32_t)best << (8 * j);
+        *lw |= (uint32_t)best << (8 * j);
         pv[j] = pb;
-        if (++x == bx) {
-            x = 0;
-            if (++y == by) y = 0, ++z;
+    }
+}
+
+// Multi-class labels: argmax over the class fields of one level (ties: the
+// lowest class index) on a box of the level.  One thread per 4 consecutive
+// outputs (x fastest), stored as one 32-bit word (labels) and one 128-bit
+// word (probabilities) where aligned: the outputs may be page-locked host
+// memory, written across the host link.
+__global__ void k_argmax(const __grid_constant__ ClassFields f, int lx, int ly, int x0, int y0, int z0, int bx,
+                         int by, int bz, uint8_t* labels, float* prob) {
+    const int64_t n = (int64_t)bx * by * bz;
+    const int64_t k0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (k0 >= n) return;
+    const int m = n - k0 < 4 ? (int)(n - k0) : 4;
+    uint32_t lw = 0;
+    float pv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (bx == lx && by == ly) {
+        // whole planes: the box is one contiguous range of the level
+        argmax4(f, (int64_t)z0 * ly * lx + k0, m, &lw, pv);
+    } else {
+        int x, y, z;
+        vox_xyz(k0, bx, by, n, &x, &y, &z);
+        for (int j = 0; j < m; ++j) {
+            uint32_t l1;
+            float p1;
+            argmax4(f, ((int64_t)(z0 + z) * ly + (y0 + y)) * lx + (x0 + x), 1, &l1, &p1);
+            lw |= l1 << (8 * j);
+            pv[j] = p1;
+            if (++x == bx) {
+                x = 0;
+                if (++y == by) y = 0, ++z;
+            }
         }
     }
     uint8_t* lo = labels + k0;
@@ -411,7 +456,7 @@ cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t bo
 
 // Argmax on a list of bricks: block (brick, plane of the brick), each thread
 // 4 consecutive voxels of a row (as k_argmax), outputs in the level's layout.
-__global__ void k_argmax_nodes(const ClassFields f, int lx, int ly, int lz, int s, int nbx, int nby,
+__global__ void k_argmax_nodes(const __grid_constant__ ClassFields f, int lx, int ly, int lz, int s, int nbx, int nby,
                                const int64_t* nodes, uint8_t* labels, float* prob) {
     const int64_t nd = nodes[blockIdx.x];
     const int bx = (int)(nd % nbx), by = (int)((nd / nbx) % nby), bz = (int)(nd / ((int64_t)nbx * nby));
@@ -426,19 +471,7 @@ __global__ void k_argmax_nodes(const ClassFields f, int lx, int ly, int lz, int 
         const int64_t i0 = ((int64_t)Z * ly + Y) * lx + X0;
         uint32_t lw = 0;
         float pv[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int j = 0; j < m; ++j) {
-            int best = 0;
-            float pb = f.P[0][i0 + j];
-            for (int c = 1; c < f.n; ++c) {
-                const float v = f.P[c][i0 + j];
-                if (v > pb) {
-                    pb = v;
-                    best = c;
-                }
-            }
-            lw |= (uint32_t)best << (8 * j);
-            pv[j] = pb;
-        }
+        argmax4(f, i0, m, &lw, pv);
         uint8_t* lo = labels + i0;
         if (m == 4 && (reinterpret_cast<uintptr_t>(lo) & 3u) == 0) {
             *reinterpret_cast<uint32_t*>(lo) = lw;

@@ -178,7 +178,8 @@ rw_status check_opts(const rw_opts& o) {
     if (!(o.beta >= 0.0f) || !(o.w_min >= 0.0f) || !(o.tol >= 0.0) || o.max_iter < 1 || o.refine_rounds < 0 ||
         (o.precision != RW_MIXED && o.precision != RW_FP64) || o.iters_per_graph < 2 || o.tile < 0 || o.tile >= N_TILES ||
         o.brick_size < 2 || !(o.expand >= 1.0f) || o.max_batch < 1 ||
-        (o.weight != RW_WEIGHT_GAUSSIAN && o.weight != RW_WEIGHT_POISSON))
+        (o.weight != RW_WEIGHT_GAUSSIAN && o.weight != RW_WEIGHT_POISSON) || o.leaf_field < RW_LEAF_AS_PYRAMID ||
+        o.leaf_field > RW_LEAF_HOST)
         return fail(RW_ERR_INVALID_ARG, "invalid rw_opts");
     return RW_OK;
 }
@@ -918,6 +919,7 @@ void rw_opts_default(rw_opts* o) {
     o->tile = RW_TILE_AUTO;
     o->batch_bricks = 1;
     o->max_batch = 8192;
+    o->leaf_field = RW_LEAF_AS_PYRAMID;
 }
 
 const char* rw_last_error(void) { return g_err.c_str(); }
@@ -1782,7 +1784,8 @@ rw_status rw_tree_create(const rw_pyramid* py, const rw_opts* opts_in, rw_tree**
         L.nbz = (d[2] + py->s - 1) / py->s;
         L.nb = (int64_t)L.nbx * L.nby * L.nbz;
         const int64_t n = (int64_t)d[0] * d[1] * d[2];
-        const bool host = py->leaf_host && k == py->K;
+        const bool host = k == py->K && (o.leaf_field == RW_LEAF_HOST ||
+                                         (o.leaf_field == RW_LEAF_AS_PYRAMID && py->leaf_host));
         void* p0 = nullptr;
         cudaError_t e = level_alloc(host, n * 4, &p0, &L.P_host);
         L.P = static_cast<float*>(p0);

@@ -211,26 +211,27 @@ def test_per_brick_sequential_equals_batched(rw):
 
 
 def test_leaf_in_host_memory_matches_hbm(rw):
-    # out-of-core placement: the leaf level (intensities and the leaf fields
-    # of the tree) in mapped host memory gives the same results, bit for bit,
-    # through a full run and an incremental update (one fixed tile: no
-    # autotuning sweeps in either run)
+    # out-of-core placement: the leaf level in mapped host memory (the
+    # intensities, with the tree's leaf field there too or in HBM; or only the
+    # tree's leaf field) gives the same results, bit for bit, through a full
+    # run and an incremental update (one fixed tile: no autotuning sweeps)
     ph = P.vessel_tree(n=96, seed=3, n_segments=30)
     xyz, val = ph["labels_xyz"], ph["labels_value"]
     n0 = len(val) // 2
     out = []
-    for host in (False, True):
+    for host, field in ((False, "pyramid"), (True, "pyramid"), (True, "hbm"), (False, "host")):
         pyr = rw.rw_build_pyramid(ph["volume"], 16, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=host)
         leaf = pyr.read_level(pyr.levels - 1)
-        tree = rw.Tree(pyr, rw.Opts(brick_size=16, beta=130.0, tol=1e-10, tile="32x8"))
+        tree = rw.Tree(pyr, rw.Opts(brick_size=16, beta=130.0, tol=1e-10, tile="32x8", leaf_field=field))
         tree.run(xyz[:n0], val[:n0])
         first = tree.read_level(pyr.levels - 1)
         tree.update_seeds(xyz[n0:], val[n0:])
         out.append((leaf, first, tree.read_level(pyr.levels - 1)))
         tree.free()
         pyr.free()
-    for a, b in zip(out[0], out[1]):
-        assert np.array_equal(a, b)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
 
 
 def _class_trees(rw, c, s, tol, prune):
