@@ -121,7 +121,8 @@ typedef struct rw_opts {
     float t_inc;           /* Sec. IV-E, default 0.01 */
     int32_t prune_hom;     /* enable hom pruning, default 1 */
     int32_t prune_dt;      /* enable dt pruning, default 1 */
-    int32_t iters_per_graph; /* PCG sweeps per captured CUDA graph (even), default 32 */
+    int32_t iters_per_graph; /* PCG sweeps per captured CUDA graph (even) with a fixed tile, default 32;
+                                the autotuner sizes graphs to about 4 ms of sweeps (8-32) */
     int32_t tile;          /* sweep tile: 0 = autotuned choice, else an RW_TILE_* value */
     int32_t batch_bricks;  /* 1: one batched launch per level (default); 0: bricks one by one */
     int32_t max_batch;     /* bricks per batched launch, default 8192 */
