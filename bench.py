@@ -38,11 +38,13 @@ SWEEP_BYTES_PER_VOXEL = 27
 KERNEL_BYTES_PER_VOXEL = 28
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sweep5
 # launch on the 256^3 workload per tile: median over the launches of each
-# tile (autotuning sweeps included) in one ncu launch list of
-# `bench.py --steps 1 --warmup 3` (profiles/launches_plain256.md); cleared when
-# the sweep kernel changes until it is captured again
+# tile in ncu launch lists of `bench.py --steps 1 --warmup 3` (autotuning
+# sweeps included; s64x14_d1 with `--tile s64x14_d1`), profiles/
+# launches_plain256.md and k_sweep5_plain256.md; cleared when the sweep kernel
+# changes until it is captured again
 SWEEP_TRAFFIC_256 = {"s32x20": 462.27e6, "s32x20_d3": 458.75e6, "s32x22_d1": 471.94e6, "s32x22": 469.76e6,
-                     "s64x11": 472.25e6, "s64x8_d1": 464.16e6, "s64x8": 455.23e6, "s64x8_d3": 454.41e6}
+                     "s64x11": 472.25e6, "s64x8_d1": 464.16e6, "s64x8": 455.23e6, "s64x8_d3": 454.41e6,
+                     "s64x14_d1": 475.83e6}
 
 
 def _workload(n):
@@ -274,8 +276,8 @@ def run(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_256.get(tile_name) if N == 256 else None,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, median over "
-                                           "the k_sweep5 launches of this tile in one launch list "
-                                           "(profiles/launches_plain256.md)",
+                                           "the k_sweep5 launches of this tile in a launch list "
+                                           "(profiles/launches_plain256.md, k_sweep5_plain256.md)",
                          "kernel": "k_sweep5 (fused PCG sweep)", "peak_source": src,
                          "algorithmic_bytes_per_launch": alg, "basis": "27 B per free voxel per sweep",
                          "kernel_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL, "launch_ms": t_launch_s * 1e3,

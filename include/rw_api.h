@@ -153,9 +153,9 @@ enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, 
        RW_TILE_S40x20 = 24, RW_TILE_S40x8 = 25,
        /* register-blocked strips of 2 voxels (padded layout, x margin 2) */
        RW_TILE_T32x20 = 26, RW_TILE_T64x11 = 27, RW_TILE_T32x12 = 28, RW_TILE_T40x20 = 29, RW_TILE_T40x8 = 30,
-       /* strips of 4 with 3 planes in flight (_D3) or 1 (_D1); 320-thread tiles with 1 */
+       /* strips of 4 with 3 planes in flight (_D3) or 1 (_D1; s64x14_d1: 320 threads) */
        RW_TILE_S32x20_D3 = 31, RW_TILE_S64x8_D3 = 32, RW_TILE_S32x22_D1 = 33, RW_TILE_S64x8_D1 = 34,
-       RW_TILE_S64x14_D1 = 35, RW_TILE_S32x28_D1 = 36 };
+       RW_TILE_S64x14_D1 = 35 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */

@@ -224,7 +224,7 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
         c = {TILE_S40x20, TILE_S40x8};
     } else {
         c = {TILE_S64x11,    TILE_S32x22,    TILE_S32x20,    TILE_S64x8,     TILE_S32x20_D3,
-             TILE_S64x8_D3,  TILE_S32x22_D1, TILE_S64x8_D1,  TILE_S64x14_D1, TILE_S32x28_D1};
+             TILE_S64x8_D3,  TILE_S32x22_D1, TILE_S64x8_D1,  TILE_S64x14_D1};
     }
     std::vector<int> ok;
     for (int t : c)

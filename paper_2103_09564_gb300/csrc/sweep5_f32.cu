@@ -22,8 +22,7 @@ namespace {
     X(32, 64, 8, 4, 224, 3, 2)    \
     X(33, 32, 22, 4, 256, 1, 2)   \
     X(34, 64, 8, 4, 224, 1, 3)    \
-    X(35, 64, 14, 4, 320, 1, 2)   \
-    X(36, 32, 28, 4, 320, 1, 2)
+    X(35, 64, 14, 4, 320, 1, 2)
 
 template <int TX, int TY, int V, int NT, int D, int MB>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
