@@ -182,6 +182,33 @@ __device__ __forceinline__ bool grid_step(unsigned* g, int it, const int* n_acti
     return *(volatile const unsigned*)&g[2 + (it & 1)] != 0u;
 }
 
+// A field of the per-system scalars; in a looped sweep other CTAs wrote it
+// in the previous iteration, so the load bypasses L1.
+template <bool CG, typename T>
+__device__ __forceinline__ T scalar_rd(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// The whole record of a system's scalars, loaded past L1 (15 independent
+// 8-byte loads), and stored back.
+__device__ __forceinline__ void scalars_load_cg(const BoxScalars* S, BoxScalars* r) {
+    static_assert(sizeof(BoxScalars) % 8 == 0, "8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(S);
+    unsigned long long w[sizeof(BoxScalars) / 8];
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(BoxScalars) / 8); ++k) w[k] = __ldcg(src + k);
+    memcpy(r, w, sizeof(BoxScalars));
+}
+
+__device__ __forceinline__ void scalars_store(BoxScalars* S, const BoxScalars& r) {
+    unsigned long long w[sizeof(BoxScalars) / 8];
+    memcpy(w, &r, sizeof(BoxScalars));
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(S);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(BoxScalars) / 8); ++k) dst[k] = w[k];
+}
+
 // Per-strip registers carried from one plane to the next.
 template <int V>
 struct StripState {
@@ -271,7 +298,6 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
     uint32_t seq = 0;      // planes issued by this CTA so far (the same in every thread)
     bool waited_out = false;
     __shared__ int s_go;
-    using SP = typename std::conditional<LOOP, volatile BoxScalars*, BoxScalars*>::type;
 
     for (int it = 0; it < (LOOP ? A.loop_iters : 1); ++it) {
     // iteration `it` reads the (u, p) copy of parity A.parity + it
@@ -286,13 +312,13 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         const int li = (int)(w / tpb);  // position in the list of active systems
         const int box = A.list ? A.list[li] : li;
         const int t = (int)(w - (int64_t)li * tpb);
-        SP S = A.sc + box;
-        if (!S->active) continue;
+        BoxScalars* S = A.sc + box;
+        if (!scalar_rd<LOOP>(&S->active)) continue;
         const int tx = t % A.ntx, ty = (t / A.ntx) % A.nty, tz = t / (A.ntx * A.nty);
-        const float alpha = (float)S->alpha;
+        const float alpha = (float)scalar_rd<LOOP>(&S->alpha);
         // p_k = ku u + bp p: u + beta p, or p itself when the direction is kept
-        const bool keep = S->phase == 2;
-        const float ku = keep ? 0.0f : 1.0f, bp = keep ? 1.0f : (float)S->beta;
+        const bool keep = scalar_rd<LOOP>(&S->phase) == 2;
+        const float ku = keep ? 0.0f : 1.0f, bp = keep ? 1.0f : (float)scalar_rd<LOOP>(&S->beta);
         int ez = A.bx.nz;
         if (A.bx.ext) ez = A.bx.ext[3 * box + 2];
         const int z0 = tz * A.zc;  // even: the chunk depth is even
@@ -490,7 +516,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
 #pragma unroll
             for (int k = 0; k < 6; ++k) pp[k] = v[k];
             __threadfence();
-            const unsigned prev = atomicAdd(const_cast<unsigned*>(&S->counter), 1u);
+            const unsigned prev = atomicAdd(&S->counter, 1u);
             s_last = (prev == (unsigned)tpb - 1u);
         }
         __syncthreads();
@@ -503,8 +529,17 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);
             block_reduce<NT, 6>(tv, red);
             if (tid == 0) {
-                S->counter = 0u;
-                finalize_box(S, tv, A.n_active, out_par);
+                if constexpr (LOOP) {
+                    // the record as other CTAs left it, updated in registers
+                    BoxScalars loc;
+                    scalars_load_cg(S, &loc);
+                    loc.counter = 0u;
+                    finalize_box(&loc, tv, A.n_active, out_par);
+                    scalars_store(S, loc);
+                } else {
+                    S->counter = 0u;
+                    finalize_box(S, tv, A.n_active, out_par);
+                }
             }
         }
         __syncthreads();
