@@ -333,7 +333,7 @@ cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, 
     return cudaGetLastError();
 }
 
-// Decide which systems iterate in this round and set their inner target:
+// Decide which systems iterate in this refinement round and set their inner target:
 // stop the round at ||r|| <= max(tol ||b||, eps_inner ||r_round_start||).
 __global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
                               int restart, int* n_active) {
