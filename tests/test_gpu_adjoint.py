@@ -59,10 +59,13 @@ def test_dense_adjoint_on_12_cubed_crop(rw):
     assert np.max(np.abs(dg.cpu().numpy() - dgo)) <= 1e-3 * np.max(np.abs(dgo))
 
 
-def test_autograd_function_batch_and_fd(rw):
+def _autograd_fd_check(rw, n, batch):
+    """Soft-Dice loss over a batch through RWSolveFn: the adjoint's gradients
+    with respect to beta and to the three largest-gradient intensities agree
+    with central finite differences."""
     import torch
     from paper_2103_09564_gb300.autograd import RWSolveFn
-    b = P.adjoint_batch(n=16, batch=4)
+    b = P.adjoint_batch(n=n, batch=batch)
     g = _cuda(b["volume"]).requires_grad_(True)
     beta = torch.tensor(130.0, device="cuda", requires_grad=True)
     code, val = _cuda(b["code"]), _cuda(b["value"])
@@ -94,3 +97,13 @@ def test_autograd_function_batch_and_fd(rw):
         with torch.no_grad():
             fdg = (loss_of(gp, beta) - loss_of(gm, beta)).item() / (2 * h)
         assert abs(gg[i] - fdg) <= 2e-2 * abs(gg).max()
+
+
+def test_autograd_function_batch_and_fd(rw):
+    _autograd_fd_check(rw, 16, 4)
+
+
+def test_autograd_full_size_batch_fd(rw):
+    # the differentiable workload at full size: 32 volumes of 96^3, as the
+    # benchmark solves them
+    _autograd_fd_check(rw, 96, 32)

@@ -110,6 +110,24 @@ def test_full_run_parity(rw, n, s, seed):
         assert st["bricks_pruned"] == ot.stats["bricks_pruned"]
 
 
+def test_brick_64_parity(rw):
+    # the 64^3 brick variant: 80^3 expanded neighbourhoods (two brick tiles
+    # across x), root 64^3, one leaf level of 8 bricks
+    ph = P.vessel_tree(n=128, seed=6, n_segments=20)
+    s = 64
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=1e-11))
+    st = tree.run(ph["labels_xyz"], ph["labels_value"])
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), s)
+    oo = hrw.Opts(brick_size=s, beta=130.0)
+    ot = hrw.run(levels, ph["labels_xyz"], ph["labels_value"], oo)
+    exc = _compare(rw, tree, ot, oo, s)
+    if not exc:
+        assert st["bricks_solved"] == ot.stats["bricks_solved"]
+        assert st["bricks_pruned"] == ot.stats["bricks_pruned"]
+
+
 def test_single_brick_equals_plain(rw):
     c = P.random_case((12, 10, 14), seed=5, seed_frac=0.05, levels=[0.0, 1.0])
     z, y, x = np.nonzero(c["code"] == 1)
