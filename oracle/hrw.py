@@ -27,6 +27,13 @@ Readings of points the paper leaves open (each mirrored by the CUDA path):
   border seeds;
 * upsampling is trilinear at u = (i + 0.5)/2 - 0.5 with clamp-to-edge;
 * a node whose box holds no seed at all keeps its initial guess.
+
+Parity unpinned: these readings, the fill of pruned holes and the similarity
+test against the filled old field are checked only by invariants (one brick
+equals the plain solve, constant volumes prune to the label value, label
+voxels exact in solved bricks, pruning changes few labels, an update without
+labels reuses everything) and by agreement with the CUDA path; the paper
+prints no values that pin them.
 """
 from __future__ import annotations
 
