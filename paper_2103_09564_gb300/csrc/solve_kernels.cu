@@ -188,7 +188,11 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                 ++nf;
                 const double gi = gdbl_w(a, i), xi = xh[i];
                 const double rh = a.rhs ? (double)a.rhs[i] : 0.0;
-                double d = 0, s = 0, b = rh;
+                // s (the operator applied to x) in FP64; the diagonal d and the
+                // right-hand side b in T: d only scales u (stored in T), b only
+                // enters ||b||, the reference of the relative stopping test
+                double s = 0;
+                T d = 0, b = (T)rh;
                 const int nbx[6] = {x - 1, x + 1, x, x, x, x};
                 const int nby[6] = {y, y, y - 1, y + 1, y, y};
                 const int nbz[6] = {z, z, z, z, z - 1, z + 1};
@@ -208,16 +212,16 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                         w = fmax(exp(a.mbeta * dg * dg), a.wmin);
                     }
                     const double xj = xh[j];
-                    d += w;
+                    d += (T)w;
                     s += w * (xi - xj);
-                    if (cj == SEED) b += w * xj;
+                    if (cj == SEED) b += (T)w * (T)xj;
                 }
                 const double r = rh - s;
-                bb += b * b;
+                bb += (double)b * (double)b;
                 rr += r * r;
                 // u is stored in T: for FP32 the quotient of the rounded
                 // operands is as accurate as the stored value
-                if constexpr (sizeof(T) == 4) uo = d > 0.0 ? (float)r / (float)d : 0.0f;
+                if constexpr (sizeof(T) == 4) uo = d > 0.0f ? (float)r / d : 0.0f;
                 else uo = d > 0.0 ? (T)(r / d) : (T)0;
             }
         }
