@@ -291,7 +291,8 @@ rw_status rw_update_seeds(rw_tree* tree, const rw_labels* added, rw_stats* stats
 /* rw_update_seeds on n_trees trees at once (e.g. one per class of a
  * multi-class labelling, Sec. III-B): added[i] (array of n_trees entries,
  * NULL: no new labels) goes to trees[i].  The result of every tree is the one
- * rw_update_seeds gives; at each level the nodes of all trees are solved in
+ * rw_update_seeds gives (up to the rounding of a differently composed batch:
+ * reduction orders differ); at each level the nodes of all trees are solved in
  * shared batched launches, so the PCG iterations of the trees run
  * concurrently.  `stats` (nullable) sums over the trees.  RW_ERR_INVALID_ARG
  * unless the trees are distinct, fully refined, on one pyramid and have equal
