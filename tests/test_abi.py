@@ -71,3 +71,25 @@ def test_invalid_arguments_rejected_on_host(lib):
     v.dims[0] = v.dims[1] = v.dims[2] = 4
     rc = lib.rw_solve(ctypes.byref(v), None, ctypes.byref(o), None, None, ctypes.byref(st), None)
     assert rc == _abi.RW_ERR_INVALID_ARG
+
+
+def test_new_entry_points_reject_bad_arguments_on_host(lib):
+    import paper_2103_09564_gb300 as rw
+    from paper_2103_09564_gb300 import _abi
+    st = _abi.rw_stats()
+    # no trees: rejected before any CUDA call
+    assert lib.rw_update_seeds_trees(None, 0, None, ctypes.byref(st), None) == _abi.RW_ERR_INVALID_ARG
+    assert lib.rw_trees_argmax_changed(None, 3, None, None, None) == _abi.RW_ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.rw_trees_argmax_changed(arr, 1, None, None, None) == _abi.RW_ERR_INVALID_ARG
+    # leaf placement names map to the header's values; an unknown value is rejected
+    assert rw.Opts(leaf_field="hbm").leaf_field == _abi.RW_LEAF_HBM
+    assert rw.Opts(leaf_field="host").leaf_field == _abi.RW_LEAF_HOST
+    assert rw.Opts().leaf_field == _abi.RW_LEAF_AS_PYRAMID
+    o = rw.Opts()
+    o.leaf_field = 7
+    v = _abi.rw_volume()
+    v.data = 1
+    v.dims[0] = v.dims[1] = v.dims[2] = 4
+    rc = lib.rw_solve(ctypes.byref(v), None, ctypes.byref(o), None, None, ctypes.byref(st), None)
+    assert rc == _abi.RW_ERR_INVALID_ARG
