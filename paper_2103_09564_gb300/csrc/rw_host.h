@@ -11,6 +11,8 @@
 #include "rw_api.h"
 #include "rw_internal.h"
 
+// Return RW_ERR_OOM / RW_ERR_CUDA (with the call and its error text) when a
+// CUDA call fails; RCK returns any status other than RW_OK.
 #define CK(call)                                                                                                 \
     do {                                                                                                         \
         cudaError_t e_ = (call);                                                                                 \
