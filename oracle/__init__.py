@@ -15,9 +15,10 @@ Contents
 
 Pins (``tests/test_oracle_*.py``): dense Cholesky on <= 8^3 voxels, closed
 forms (voltage divider, linear ramp), the discrete maximum principle,
-multi-class sum-to-one, symmetry, bit-exact pyramid cases, single-brick
-hierarchy == plain solve, pruning agreement, B^(2/3) growth, finite
-differences for the adjoint.
+multi-class sum-to-one, symmetry, the residual against a dense operator,
+bit-exact pyramid cases, single-brick hierarchy == plain solve, tiny trees
+and incremental passes rebuilt independently with dense Cholesky node solves,
+pruning agreement, B^(2/3) growth, finite differences for the adjoint.
 """
 from __future__ import annotations
 

@@ -28,12 +28,21 @@ Readings of points the paper leaves open (each mirrored by the CUDA path):
 * upsampling is trilinear at u = (i + 0.5)/2 - 0.5 with clamp-to-edge;
 * a node whose box holds no seed at all keeps its initial guess.
 
-Parity unpinned: these readings, the fill of pruned holes and the similarity
-test against the filled old field are checked only by invariants (one brick
-equals the plain solve, constant volumes prune to the label value, label
-voxels exact in solved bricks, pruning changes few labels, an update without
-labels reuses everything) and by agreement with the CUDA path; the paper
-prints no values that pin them.
+Pins (tests/test_oracle_hier_pins.py): every node problem, decision and
+field of tiny trees (s = 4 with e = 1.25, 1.5, 1.75; uneven dims; conflicts;
+user seeds on border layers; hom and dt pruning; absent nodes) and of
+incremental passes is rebuilt there independently -- neighbourhoods as index
+ranges, the border layer as the voxels with a neighbour outside N(n), the
+upsampling as tent functions, every node solved by dense Cholesky -- and must
+match this module to 1e-12 and decision for decision; hand cases fix the
+margins, the strict hom / dt predicates, a conflict with an added label that
+forces a re-solve, and a similar node whose subtree is kept bit for bit while
+its siblings re-solve; planted one-line mistakes in margins, _region,
+_solve_node (border faces, precedence), upsample, _flags and update each fail
+them.  The readings themselves (trilinear upsampling, the border layer, the
+fill of pruned holes, similarity against the filled old field) are choices
+where the paper is silent; the pins fix that this module computes them as
+stated above.
 """
 from __future__ import annotations
 

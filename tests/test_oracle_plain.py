@@ -238,3 +238,50 @@ def test_poisson_voltage_divider():
     x, it, rr, st = O.rw_solve(g, code, xin, S, kind="poisson")
     w1, w2 = math.exp(-0.5 * (4 - 5) ** 2), math.exp(-0.5 * (5 - 7) ** 2)
     assert st == 0 and abs(x[0, 0, 1] - w2 / (w1 + w2)) <= 1e-12
+
+
+def _dense_laplacian(g, code, beta, w_min=1e-30):
+    """Graph Laplacian of the 6-connected grid (Sec. III-B) without absent vertices, dense."""
+    n = g.size
+    L = np.zeros((n, n))
+    idx = np.arange(n).reshape(g.shape)
+    cf, gf = code.ravel(), g.ravel()
+    for axis in range(3):
+        a = np.moveaxis(idx, axis, 0)[:-1].ravel()
+        b = np.moveaxis(idx, axis, 0)[1:].ravel()
+        keep = (cf[a] != 2) & (cf[b] != 2)
+        a, b = a[keep], b[keep]
+        w = np.maximum(np.exp(-beta * (gf[a] - gf[b]) ** 2), w_min)
+        np.add.at(L, (a, a), w)
+        np.add.at(L, (b, b), w)
+        np.add.at(L, (a, b), -w)
+        np.add.at(L, (b, a), -w)
+    return L
+
+
+def test_residual_matches_dense_operator():
+    # r = b - A x on the free vertices with b = -B^T x_M (+ an extra
+    # right-hand side), A = L_U: written out with the dense Laplacian
+    c = P.random_case((5, 6, 7), seed=14, seed_frac=0.15)
+    code = c["code"].copy()
+    code[1:3, 2:4, 4:6] = 2
+    g = O.dequantize(O.quantize(c["volume"]))
+    beta = 25.0
+    x = P.uniform(14, 70, np.arange(g.size, dtype=np.uint64)).reshape(g.shape)
+    x = np.where(code == 1, c["value"], x)
+    extra = P.uniform(14, 71, np.arange(g.size, dtype=np.uint64)).reshape(g.shape) - 0.5
+    L = _dense_laplacian(g, code, beta)
+    U = np.flatnonzero(code.ravel() == 0)
+    M = np.flatnonzero(code.ravel() == 1)
+    xf = x.ravel()
+    for rhs in (None, extra):
+        b = -L[np.ix_(U, M)] @ xf[M] + (0.0 if rhs is None else rhs.ravel()[U])
+        want = np.zeros(g.size)
+        want[U] = b - L[np.ix_(U, U)] @ xf[U]
+        r, bn = O.residual(g, code, x, beta, rhs=rhs)
+        assert np.max(np.abs(r.ravel() - want)) <= 1e-13
+        assert bn == pytest.approx(np.linalg.norm(b), rel=1e-14)
+    # at the dense solution the residual vanishes
+    xs = _dense_reference(g, code, np.where(code == 1, c["value"], 0.0), beta)
+    r, bn = O.residual(g, code, xs, beta)
+    assert np.max(np.abs(r)) <= 1e-13 * bn
