@@ -35,7 +35,8 @@ typedef enum rw_status {
     RW_ERR_INVALID_ARG = 1,    /* bad pointer, size, dtype or option */
     RW_ERR_NO_SEEDS = 2,       /* a system without any seed has no unique solution */
     RW_ERR_NOT_CONVERGED = 3,  /* max_iter reached before the tolerance */
-    RW_ERR_TIMEOUT = 4,        /* reserved: no kernel of this library waits on a flag */
+    RW_ERR_TIMEOUT = 4,        /* a bounded wait inside a sweep kernel (a TMA load, a grid barrier)
+                                  ran out: the kernel stopped waiting, flagged it and returned */
     RW_ERR_OOM = 5,            /* device allocation failed */
     RW_ERR_CUDA = 6,           /* a CUDA runtime call failed */
     RW_ERR_UNIMPLEMENTED = 7
@@ -209,17 +210,19 @@ rw_status rw_solve(const rw_volume* vol, const rw_seed_mask* seeds, const rw_opt
  * synchronise the whole device), a plug-in inside a host application that
  * owns the GPU memory budget, a service that fixes its footprint at start-up.
  * This entry point allocates nothing: its scratch is one file-scope device
- * array of about 10.5 MB that every GPU loading the library keeps until the
+ * array of about 12.1 MB that every GPU loading the library keeps until the
  * process exits.  Same arguments and results as rw_solve, with these
  * differences:
- *  - every array must be device memory (no host staging);
+ *  - every array must be device memory of the current device, or managed
+ *    memory (no host staging); anything else is RW_ERR_INVALID_ARG;
  *  - at most RW_NOALLOC_MAX_VOXELS voxels in total and RW_NOALLOC_MAX_BATCH
  *    volumes; larger inputs are rejected with RW_ERR_INVALID_ARG;
  *  - opts->precision must be RW_MIXED and vol->storage RW_STORE_UNORM16; a
  *    system that FP32 sweeps cannot resolve returns RW_ERR_NOT_CONVERGED
  *    (rw_solve would finish it with FP64 sweeps);
  *  - work runs on `stream` itself (no internal stream, CUDA graph or timing
- *    event) and the stream is synchronised before returning.
+ *    event); the call synchronises the stream before it returns, and also
+ *    between sweeps, where it reads the count of active systems on the host.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, once per device); make that first call before any
  * stream capture.  All calls share the array and each call clears what must

@@ -168,25 +168,37 @@ def rw_solve(volume, code, value=None, opts=None, x0=None, out=None, *, lo=0.0, 
 def rw_solve_noalloc(volume, code, value=None, opts=None, x0=None, out=None, *, lo=0.0, hi=1.0, normalize=False,
                      stream=None):
     """rw_solve for callers that cannot allocate device memory: every array
-    must already live on the GPU (CUDA tensors, `out` included when given),
-    the scratch is the library's fixed device array (at most
-    RW_NOALLOC_MAX_VOXELS voxels).  Runs on `stream` (default: the current
-    torch stream).  Returns (x, stats)."""
+    must already live on the volume's GPU (CUDA tensors, `out` included when
+    given; without `out` this wrapper allocates the result tensor, the
+    library call itself allocates nothing), the scratch is the library's
+    fixed device array (at most RW_NOALLOC_MAX_VOXELS voxels).  The call runs
+    with the volume's device current, on `stream` (a torch.cuda.Stream or a
+    raw cudaStream_t handle; default: that device's current torch stream).
+    Returns (x, stats)."""
     torch = _torch()
     batch = len(volume.shape) == 4
     v, va, shp = _volume(volume, lo, hi, normalize, RW_STORE_UNORM16, batch)
     c = _Arr(code, np.uint8)
     val = _Arr(value, np.float32)
     xi = _Arr(x0, np.float32)
+    dev = volume.device if hasattr(volume, "device") and getattr(volume, "is_cuda", False) else None
     if out is None:
-        out = torch.empty(tuple(volume.shape), dtype=torch.float32, device=volume.device)
+        out = torch.empty(tuple(volume.shape), dtype=torch.float32, device=dev if dev is not None else "cpu")
     o = _Arr(out)
     sm = _abi.rw_seed_mask(c.ptr, val.ptr)
     st = _abi.rw_stats()
     opts = opts if opts is not None else Opts()
-    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
-    rc = load().rw_solve_noalloc(ctypes.byref(v), ctypes.byref(sm), ctypes.byref(opts), xi.ptr, o.ptr,
-                                 ctypes.byref(st), s)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream if dev is not None else 0
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    if dev is not None:
+        with torch.cuda.device(dev):
+            rc = load().rw_solve_noalloc(ctypes.byref(v), ctypes.byref(sm), ctypes.byref(opts), xi.ptr, o.ptr,
+                                         ctypes.byref(st), ctypes.c_void_p(stream))
+    else:
+        rc = load().rw_solve_noalloc(ctypes.byref(v), ctypes.byref(sm), ctypes.byref(opts), xi.ptr, o.ptr,
+                                     ctypes.byref(st), ctypes.c_void_p(stream))
     _check(rc)
     d = st.as_dict()
     d["status"] = rc

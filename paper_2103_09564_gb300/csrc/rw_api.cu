@@ -448,7 +448,7 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
         *sweeps += done;
         n_act = w->pinned[0];
         if (w->pinned[1]) {
-            st = fail(RW_ERR_CUDA, "PCG sweep: a load or grid-barrier wait ran out (tile %d)", cfg.tile);
+            st = fail(RW_ERR_TIMEOUT, "PCG sweep: a load or grid-barrier wait ran out (tile %d)", cfg.tile);
             break;
         }
         if (done <= 0) {

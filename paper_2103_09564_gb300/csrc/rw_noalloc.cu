@@ -17,9 +17,12 @@
 //
 // The first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (once per device, with that device current); make that
-// first call before any stream capture.  Every call uses the same array and
-// leaves its contents behind: the call clears what must start at zero, and
-// calls that overlap on the GPU (other streams, other threads) race.
+// first call before any stream capture.  Every call synchronises `stream`
+// before it returns (it reads the active-system count on the host between
+// sweeps).  Every call uses the same array and leaves its contents behind:
+// the call clears what must start at zero, and calls that overlap on the GPU
+// (other streams, other threads) race.  Every array must live on the current
+// device (or be managed memory): the kernels run there.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -57,8 +60,10 @@ constexpr size_t kOffSP = al(kOffRP + kRPart);                      // sweep par
 constexpr size_t kOffSC = al(kOffSP + kMaxItems * 6 * sizeof(double));  // BoxScalars
 constexpr size_t kOffNA = al(kOffSC + kMaxBatch * sizeof(BoxScalars));   // active count
 constexpr size_t kScratchBytes = al(kOffNA + 256);
+// the documented size ("about 12.1 MB") must stay true
+static_assert(kScratchBytes > 12000000 && kScratchBytes < 12200000, "update the documented scratch size");
 
-// The scratch array (about 10.5 MB).
+// The scratch array (about 12.1 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mu;
@@ -83,14 +88,17 @@ rw_status fail_cuda(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return fail_cuda(e_, #call); \
     } while (0)
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (the current one, where the kernels run) or
+// managed memory.
+bool on_device(const void* p, int dev) {
     if (!p) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    return at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -124,15 +132,16 @@ extern "C" rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* 
                  (long long)ntot, (long long)batch, (long long)kMaxVoxels, (long long)kMaxBatch);
         return fail(RW_ERR_INVALID_ARG, buf);
     }
-    if (!on_device(vol->data) || !on_device(seeds->code) || !on_device(x_out) ||
-        (seeds->value && !on_device(seeds->value)) || (x0 && !on_device(x0)))
-        return fail(RW_ERR_INVALID_ARG, "rw_solve_noalloc: every array must be device memory");
-    cudaStream_t s = static_cast<cudaStream_t>(stream_v);
-
-    // set-up, once per device: the device address of the scratch array
     int dev = 0;
     NCK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return fail(RW_ERR_INVALID_ARG, "rw_solve_noalloc: device index out of range");
+    if (!on_device(vol->data, dev) || !on_device(seeds->code, dev) || !on_device(x_out, dev) ||
+        (seeds->value && !on_device(seeds->value, dev)) || (x0 && !on_device(x0, dev)))
+        return fail(RW_ERR_INVALID_ARG,
+                    "rw_solve_noalloc: every array must be device memory of the current device (or managed)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream_v);
+
+    // set-up, once per device: the device address of the scratch array
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_setup_mu);

@@ -164,17 +164,23 @@ def _voxel_noise(seed, stream, shape, sigma, slab=1 << 22):
 
 
 def ball_case(n: int = 64, seed: int = 0, radius: float = 20.0, bg: float = 0.3, fg: float = 0.7,
-              sigma: float = 0.1, ellipsoid: bool = False):
+              sigma: float = 0.1, ellipsoid: bool = False, shape=None):
     """Ball (or one random ellipsoid) on a background with i.i.d. Gaussian noise.
 
     Foreground seeds: a 9-voxel line along x through the centre voxel row
     ``y = z = n // 2``; background seeds: every voxel of the six border faces.
+    ``shape`` (z, y, x), when given, replaces the n^3 box: the object is
+    centred in it and the seed line runs through its centre row.
     Returns a dict with ``volume`` (float32, clamped to [0, 1]), ``code``,
     ``value`` and the analytic ``mask`` (voxel centre inside the object).
     """
-    shape = (n, n, n)
+    if shape is None:
+        shape = (n, n, n)
     x, y, z = _centres(shape)
     c = n / 2.0
+    if shape != (n, n, n):
+        cz, cy, cx = (d / 2.0 for d in shape)
+        x, y, z = x - (cx - c), y - (cy - c), z - (cz - c)
     if ellipsoid:
         st = Stream(seed, 7)
         R = st.rotation()
@@ -191,10 +197,11 @@ def ball_case(n: int = 64, seed: int = 0, radius: float = 20.0, bg: float = 0.3,
     code = np.zeros(shape, dtype=np.uint8)
     value = np.zeros(shape, dtype=np.float32)
     code[border_faces(shape)] = 1
-    h = n // 2
-    a, b = max(h - 4, 1), min(h + 5, n - 1)
-    code[h, h, a:b] = 1
-    value[h, h, a:b] = 1.0
+    hz, hy, hx = (d // 2 for d in shape)
+    a, b = max(hx - 4, 1), min(hx + 5, shape[2] - 1)
+    if 0 < hz < shape[0] - 1 and 0 < hy < shape[1] - 1:
+        code[hz, hy, a:b] = 1
+        value[hz, hy, a:b] = 1.0
     return {"volume": vol, "code": code, "value": value, "mask": mask, "beta": 130.0}
 
 

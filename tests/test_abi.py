@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -93,3 +94,21 @@ def test_new_entry_points_reject_bad_arguments_on_host(lib):
     v.dims[0] = v.dims[1] = v.dims[2] = 4
     rc = lib.rw_solve(ctypes.byref(v), None, ctypes.byref(o), None, None, ctypes.byref(st), None)
     assert rc == _abi.RW_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_65_volumes_on_host(lib):
+    # the fixed scratch holds at most RW_NOALLOC_MAX_BATCH volumes: a batch of
+    # 65 tiny volumes is refused before any CUDA call
+    from paper_2103_09564_gb300 import _abi
+    v = _abi.rw_volume()
+    h = np.zeros((65, 2, 2, 2), np.float32)
+    v.data = h.ctypes.data
+    v.dims[0] = v.dims[1] = v.dims[2] = 2
+    v.batch = 65
+    hc = np.ones((65, 2, 2, 2), np.uint8)
+    sm = _abi.rw_seed_mask(hc.ctypes.data, None)
+    out = np.zeros((65, 2, 2, 2), np.float32)
+    st = _abi.rw_stats()
+    rc = lib.rw_solve_noalloc(ctypes.byref(v), ctypes.byref(sm), None, None, out.ctypes.data, ctypes.byref(st), None)
+    assert rc == _abi.RW_ERR_INVALID_ARG
+    assert b"exceed" in lib.rw_last_error() and b"65 volume" in lib.rw_last_error()

@@ -34,7 +34,7 @@ def test_adjoint_matches_oracle(rw, n, seed, beta):
     opts = rw.Opts(beta=beta, tol=1e-10)
     x, _ = rw.rw_solve(_cuda(c["volume"]), _cuda(c["code"]), _cuda(c["value"]), opts, storage=rw.RW_STORE_F32)
     dg, db, st = rw.rw_solve_adjoint(_cuda(c["volume"]), _cuda(c["code"]), x, _cuda(dl.astype(np.float32)), opts)
-    assert abs(db[0] - dbo) <= 1e-3 * abs(dbo)
+    assert abs(db[0] - dbo) <= 1e-4 * abs(dbo)
     assert np.max(np.abs(dg.cpu().numpy() - dgo)) <= 1e-3 * np.max(np.abs(dgo))
 
 
@@ -55,14 +55,50 @@ def test_dense_adjoint_on_12_cubed_crop(rw):
     opts = rw.Opts(beta=beta, tol=1e-11)
     x, _ = rw.rw_solve(_cuda(vol), _cuda(code), _cuda(val), opts, storage=rw.RW_STORE_F32)
     dg, db, _ = rw.rw_solve_adjoint(_cuda(vol), _cuda(code), x, _cuda(dl.astype(np.float32)), opts)
-    assert abs(db[0] - dbo) <= 1e-3 * abs(dbo)
+    assert abs(db[0] - dbo) <= 1e-4 * abs(dbo)
     assert np.max(np.abs(dg.cpu().numpy() - dgo)) <= 1e-3 * np.max(np.abs(dgo))
+
+
+def _oracle_loss(g, code, value, beta, mask):
+    x, _, _, st = O.rw_solve(g, code, np.where(code == 1, value, 0.0), beta, tol=1e-14)
+    assert st in (0, 3)
+    return OA.soft_dice(x, mask)[0]
+
+
+@pytest.mark.parametrize("n,seed", [(16, 0), (20, 3)])
+def test_adjoint_matches_oracle_finite_differences(rw, n, seed):
+    # central differences of the FP64 oracle's forward solve (step 1e-3): the
+    # GPU adjoint's dl/dbeta within 1e-4 relative, dl/dg within 1e-3 of
+    # max |dl/dg| at a spread of free voxels and at the largest one
+    c = P.ball_case(n=n, seed=seed, radius=0.3 * n, ellipsoid=(seed % 2 == 1))
+    beta, h = 130.0, 1e-3
+    g = c["volume"].astype(np.float64)
+    xo, _, _, _ = O.rw_solve(g, c["code"], np.where(c["code"] == 1, c["value"], 0.0), beta, tol=1e-14)
+    _, dl = OA.soft_dice(xo, c["mask"])
+    opts = rw.Opts(beta=beta, tol=1e-10)
+    x, _ = rw.rw_solve(_cuda(c["volume"]), _cuda(c["code"]), _cuda(c["value"]), opts, storage=rw.RW_STORE_F32)
+    dg, db, _ = rw.rw_solve_adjoint(_cuda(c["volume"]), _cuda(c["code"]), x, _cuda(dl.astype(np.float32)), opts)
+    dg = dg.cpu().numpy().astype(np.float64)
+    fd_b = (_oracle_loss(g, c["code"], c["value"], beta + h, c["mask"]) -
+            _oracle_loss(g, c["code"], c["value"], beta - h, c["mask"])) / (2 * h)
+    assert abs(db[0] - fd_b) <= 1e-4 * abs(fd_b)
+    scale = np.max(np.abs(dg))
+    free = np.flatnonzero(c["code"].ravel() == 0)
+    for v in list(free[:: max(1, len(free) // 10)]) + [int(np.argmax(np.abs(dg)))]:
+        gp = g.copy().ravel(); gp[v] += h
+        gm = g.copy().ravel(); gm[v] -= h
+        fd = (_oracle_loss(gp.reshape(g.shape), c["code"], c["value"], beta, c["mask"]) -
+              _oracle_loss(gm.reshape(g.shape), c["code"], c["value"], beta, c["mask"])) / (2 * h)
+        assert abs(fd - dg.ravel()[v]) <= 1e-3 * scale
 
 
 def _autograd_fd_check(rw, n, batch):
     """Soft-Dice loss over a batch through RWSolveFn: the adjoint's gradients
     with respect to beta and to the three largest-gradient intensities agree
-    with central finite differences."""
+    with central finite differences of the GPU forward solve.  Its FP32
+    output limits these differences (a one-voxel step of 2^-10 moves the loss
+    by little more than the output's rounding), hence the looser bounds; the
+    FP64 differences of the oracle pin the adjoint to 1e-4 / 1e-3 above."""
     import torch
     from paper_2103_09564_gb300.autograd import RWSolveFn
     b = P.adjoint_batch(n=n, batch=batch)

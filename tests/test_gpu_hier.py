@@ -11,8 +11,10 @@ from oracle import hrw
 pytestmark = pytest.mark.gpu
 # Brick systems can hold weakly coupled pockets (isolated eigenvalues of the
 # Jacobi-scaled matrix near 1e-6): there a relative residual of 1e-9 still
-# allows 1e-3 of error, so the parity runs solve every brick to 1e-11.
+# allows 1e-3 of error.  The parity runs solve every brick to 1e-10, the
+# tolerance the hierarchical benchmarks run at.
 TOL = 1e-4
+HIER_TOL = 1e-10
 NEAR = 1e-4      # a pruning decision may differ only this close to its threshold
 
 
@@ -77,6 +79,9 @@ def _compare(rw, tree, otree, opts, s, incremental=False):
                  max(lo[2] - 2 * s, 0):hi[2] + 2 * s] = False
         err = np.max(np.abs(field - otree.P[k])[mask]) if mask.any() else 0.0
         assert err <= TOL, f"level {k}: max |gpu - oracle| = {err}"
+        # thresholded labels agree wherever the oracle is clear of 0.5
+        clear = mask & (np.abs(otree.P[k] - 0.5) > 1e-3)
+        assert np.array_equal(field[clear] > 0.5, otree.P[k][clear] > 0.5), f"level {k}: labels differ"
     return excluded
 
 
@@ -97,7 +102,7 @@ def test_full_run_parity(rw, n, s, seed):
     else:
         ph = P.vessel_tree(n=n, seed=seed, n_segments=30)
     pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
-    opts = rw.Opts(brick_size=s, beta=130.0, tol=1e-11)
+    opts = rw.Opts(brick_size=s, beta=130.0, tol=HIER_TOL)
     tree = rw.Tree(pyr, opts)
     st = tree.run(ph["labels_xyz"], ph["labels_value"])
     q = O.quantize(ph["volume"], 0.0, 5000.0, True)
@@ -116,7 +121,7 @@ def test_brick_64_parity(rw):
     ph = P.vessel_tree(n=128, seed=6, n_segments=20)
     s = 64
     pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
-    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=1e-11))
+    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=HIER_TOL))
     st = tree.run(ph["labels_xyz"], ph["labels_value"])
     q = O.quantize(ph["volume"], 0.0, 5000.0, True)
     levels = O.pyramid(O.leaf_level(q), s)
@@ -134,36 +139,49 @@ def test_single_brick_equals_plain(rw):
     xyz = np.stack([x + 0.5, y + 0.5, z + 0.5], 1)
     val = c["value"][z, y, x]
     pyr = rw.rw_build_pyramid(c["volume"], 16)
-    tree = rw.Tree(pyr, rw.Opts(brick_size=16, beta=30.0, tol=1e-11))
+    tree = rw.Tree(pyr, rw.Opts(brick_size=16, beta=30.0, tol=HIER_TOL))
     tree.run(xyz, val)
     leaf = O.leaf_level(O.quantize(c["volume"]))
     xo, _, _, _ = O.rw_solve(leaf.astype(np.float64), c["code"], c["value"], 30.0)
     assert np.max(np.abs(tree.read_level(0) - xo)) <= 1e-6
 
 
-def test_no_pruning_parity_and_agreement(rw):
-    ph = P.vessel_tree(n=64, seed=6, n_segments=30)
+@pytest.mark.parametrize("seed", [2, 6])
+def test_no_pruning_parity_and_agreement(rw, seed):
+    # Table IV: pruning leaves the segmentation essentially unchanged.  Both
+    # GPU trees (pruned, unpruned) match the oracle's, and the share of labels
+    # that pruning flips on the GPU equals the method's own (the oracle's) on
+    # this phantom.  On seed 2 that share is below 0.1 % (the oracle pin's
+    # bound); on seed 6 (64^3, brick 8: thin vessels that coarse levels blur)
+    # the method itself flips 0.43 % of the labels.
+    ph = P.vessel_tree(n=64, seed=seed, n_segments=30)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    t1 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11, prune_hom=0, prune_dt=0))
+    t1 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL, prune_hom=0, prune_dt=0))
     t1.run(ph["labels_xyz"], ph["labels_value"])
-    t2 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11))
+    t2 = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL))
     s2 = t2.run(ph["labels_xyz"], ph["labels_value"])
     a, b = t1.read_level(pyr.levels - 1), t2.read_level(pyr.levels - 1)
     assert s2["bricks_pruned"] > 0
-    # Table IV: pruning leaves the binary result essentially unchanged
-    assert np.mean((a > 0.5) == (b > 0.5)) >= 0.99
     q = O.quantize(ph["volume"], 0.0, 5000.0, True)
     levels = O.pyramid(O.leaf_level(q), 8)
     oo = hrw.Opts(brick_size=8, beta=130.0, prune_hom=False, prune_dt=False)
     ot = hrw.run(levels, ph["labels_xyz"], ph["labels_value"], oo)
+    op = hrw.Opts(brick_size=8, beta=130.0)
+    ot2 = hrw.run(levels, ph["labels_xyz"], ph["labels_value"], op)
     _compare(rw, t1, ot, oo, 8)
+    _compare(rw, t2, ot2, op, 8)
+    agree = np.mean((a > 0.5) == (b > 0.5))
+    o_agree = np.mean((ot.P[-1] > 0.5) == (ot2.P[-1] > 0.5))
+    assert abs(agree - o_agree) <= 1e-4
+    if seed == 2:
+        assert agree >= 0.999
 
 
 def test_incremental_update_parity(rw):
     ph = P.vessel_tree(n=64, seed=7, n_segments=30)
     n0 = len(ph["labels_value"]) - 6
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-11)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL)
     tree = rw.Tree(pyr, opts)
     tree.run(ph["labels_xyz"][:n0], ph["labels_value"][:n0])
     su = tree.update_seeds(ph["labels_xyz"][n0:], ph["labels_value"][n0:])
@@ -186,7 +204,7 @@ def test_chained_updates_parity(rw):
     xyz, val = ph["labels_xyz"], ph["labels_value"]
     cuts = [len(val) - 9, len(val) - 6, len(val) - 3, len(val)]
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-11)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL)
     tree = rw.Tree(pyr, opts)
     tree.run(xyz[:cuts[0]], val[:cuts[0]])
     q = O.quantize(ph["volume"], 0.0, 5000.0, True)
@@ -206,7 +224,7 @@ def test_chained_updates_parity(rw):
 def test_update_without_labels_keeps_everything(rw):
     ph = P.vessel_tree(n=32, seed=3, n_segments=10)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11))
+    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL))
     tree.run(ph["labels_xyz"], ph["labels_value"])
     before = tree.read_level(pyr.levels - 1).copy()
     su = tree.update_seeds(np.zeros((0, 3)), np.zeros(0))
@@ -217,9 +235,9 @@ def test_update_without_labels_keeps_everything(rw):
 def test_per_brick_sequential_equals_batched(rw):
     ph = P.vessel_tree(n=64, seed=8, n_segments=20)
     pyr = rw.rw_build_pyramid(ph["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    a = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11))
+    a = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL))
     a.run(ph["labels_xyz"], ph["labels_value"])
-    b = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-11, batch_bricks=0, precision="fp64"))
+    b = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL, batch_bricks=0, precision="fp64"))
     b.run(ph["labels_xyz"], ph["labels_value"])
     q = O.quantize(ph["volume"], 0.0, 5000.0, True)
     det = determined_mask(O.leaf_level(q), 130.0)
@@ -267,7 +285,7 @@ def test_multiclass_argmax_matches_oracle(rw):
     # one and the fused argmax agrees with the oracle's per-class hierarchy on
     # every voxel where the two best classes are more than 1e-3 apart
     c = P.multiclass_case((64, 64, 64), seed=1, n_segments=20, n_blobs=30, n_updates=0)
-    pyr, trees = _class_trees(rw, c, 8, 1e-11, prune=False)
+    pyr, trees = _class_trees(rw, c, 8, HIER_TOL, prune=False)
     labels, pmax = rw.trees_argmax(trees, prob=np.empty((64, 64, 64), np.float32))
     fields = np.stack([t.read_level(pyr.levels - 1) for t in trees])
     assert np.array_equal(labels, np.argmax(fields, axis=0).astype(np.uint8))
@@ -380,7 +398,7 @@ def test_update_trees_matches_oracle_and_sequential_updates(rw):
     # and fields as updating the trees one by one
     c = P.multiclass_case((64, 64, 64), seed=5, n_segments=20, n_blobs=20, n_updates=2)
     pyr = rw.rw_build_pyramid(c["volume"], 8, lo=0.0, hi=5000.0, normalize=True)
-    opts = rw.Opts(brick_size=8, beta=130.0, tol=1e-11, prune_hom=1, prune_dt=0)
+    opts = rw.Opts(brick_size=8, beta=130.0, tol=HIER_TOL, prune_hom=1, prune_dt=0)
     joint = [rw.Tree(pyr, opts) for _ in range(3)]
     seq = [rw.Tree(pyr, opts) for _ in range(3)]
     q = O.quantize(c["volume"], 0.0, 5000.0, True)
@@ -415,7 +433,7 @@ def test_update_trees_matches_oracle_and_sequential_updates(rw):
         assert np.max(np.abs(a - b)[det]) <= TOL
     with pytest.raises(rw.RWError):
         rw.update_trees([joint[0], joint[0]], c["updates"][0][0], [vals[0], vals[0]])
-    other = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-10, prune_hom=1, prune_dt=0))
+    other = rw.Tree(pyr, rw.Opts(brick_size=8, beta=130.0, tol=1e-9, prune_hom=1, prune_dt=0))
     other.run(*P.class_labels(c["strokes"], 0))
     with pytest.raises(rw.RWError):
         rw.update_trees([joint[0], other], c["updates"][0][0], [vals[0], vals[1]])
@@ -430,7 +448,7 @@ def test_poisson_weights_hierarchy_parity(rw):
     val = np.array([1.0] * 9 + [0.0] * 8, np.float32)
     xyz = np.array(xyz)
     pyr = rw.rw_build_pyramid(c["volume"], 8, lo=0.0, hi=S, normalize=True)
-    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=S, tol=1e-11, weight="poisson"))
+    tree = rw.Tree(pyr, rw.Opts(brick_size=8, beta=S, tol=HIER_TOL, weight="poisson"))
     tree.run(xyz, val)
     q = O.quantize(c["volume"], 0.0, S, True)
     levels = O.pyramid(O.leaf_level(q), 8)
@@ -452,8 +470,8 @@ class _At:
 
 def test_vessel_tree_1024_sampled_bricks_and_properties(rw):
     """The 1024^3 vessel-tree workload with brick 32, in the benchmark's launch
-    configuration (batched levels, autotuned tiles; bricks solved to 1e-11 as
-    in every hierarchy parity test).  Properties of the whole result: every
+    configuration (batched levels, autotuned tiles; bricks solved to 1e-10 as
+    in the benchmark and every hierarchy parity test).  Properties of the whole result: every
     level within [0, 1] (maximum principle) and every label voxel of the leaf
     exact where its leaf brick was solved (pruned bricks hold the upsampled
     parent).  Sampled parity: leaf bricks equal the oracle's FP64 solve of the
@@ -467,7 +485,7 @@ def test_vessel_tree_1024_sampled_bricks_and_properties(rw):
     val = np.asarray(ph["labels_value"], dtype=np.float32)
     vol = ph["volume"]
     pyr = rw.rw_build_pyramid(vol, s, lo=0.0, hi=5000.0, normalize=True)
-    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=1e-11))
+    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=130.0, tol=HIER_TOL))
     tree.run(xyz, val)
     K = pyr.levels - 1
     for k in range(K + 1):
