@@ -7,7 +7,14 @@ free voxels x PCG iterations, divided by the device time (CUDA events, max
 over ranks).  The 256^3 working set streamed per sweep (about 470 MB) is
 larger than L2, so no flush is needed between steps.
 
+Beside the headline (one GPU, rank 0): the FP64 oracle's solve of the same
+system, run on the host cores in a spawned process while the GPU works, gives
+max_abs_err_vs_oracle for the timed step's output; `secondary` holds the
+hierarchical 1024^3 vessel-tree workload (brick 32) with its roofline and the
+batched mixed-precision vs per-brick FP64 comparison on its own leaf level.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload plain|hier|adjoint|multiclass]
 
 --impl reference times the FP64 CPU oracle (test infrastructure, as it
 stands) on the host cores: each step is a bounded number of its PCG
@@ -37,14 +44,30 @@ TOL = 1e-8
 SWEEP_BYTES_PER_VOXEL = 27
 KERNEL_BYTES_PER_VOXEL = 28
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sweep5
-# launch on the 256^3 workload per tile: median over the launches of each
-# tile in ncu launch lists of `bench.py --steps 1 --warmup 3` (autotuning
-# sweeps included; s64x14_d1 with `--tile s64x14_d1`), profiles/
-# launches_plain256.md and k_sweep5_plain256.md; cleared when the sweep kernel
-# changes until it is captured again
-SWEEP_TRAFFIC_256 = {"s32x20": 462.27e6, "s32x20_d3": 458.75e6, "s32x22_d1": 471.94e6, "s32x22": 469.76e6,
-                     "s64x11": 472.25e6, "s64x8_d1": 464.16e6, "s64x8": 455.23e6, "s64x8_d3": 454.41e6,
-                     "s64x14_d1": 475.83e6}
+# launch on the 256^3 workload, per tile: median over an ncu launch list of
+# `bench.py --steps 1 --warmup 3` (autotuning sweeps included).  Valid only
+# for the strip-sweep sources they were measured on (SHA-256 of the files
+# below, first 16 hex digits); any other source gives traffic null.
+SWEEP_SOURCES = ("paper_2103_09564_gb300/csrc/sweep5_kernel.cuh", "paper_2103_09564_gb300/csrc/sweep5_f32.cu")
+SWEEP_TRAFFIC_256 = {"sha": "66972cfa6d102de5",
+                     "bytes": {"s32x20_d3": 457.2e6, "s32x20": 460.1e6, "s64x8": 455.4e6, "s64x8_d3": 454.5e6,
+                               "s32x22_d1": 471.9e6, "s64x8_d1": 462.9e6, "s32x22": 469.8e6, "s64x11": 472.8e6,
+                               "s64x14_d1": 482.5e6}}
+
+
+def _sweep_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _sweep_traffic(tile_name, n):
+    if n != 256 or SWEEP_TRAFFIC_256["sha"] != _sweep_source_sha():
+        return None
+    return SWEEP_TRAFFIC_256["bytes"].get(tile_name)
 
 
 def _workload(n):
@@ -152,6 +175,61 @@ def _cpu_baseline(c, seconds=15.0):
                       f"{dt:.1f} s incl. weight set-up"}
 
 
+def _oracle_solve_child(n, threads, path):
+    """Child process (spawned): the FP64 oracle's solve of the benchmark system
+    as it stands (tol 1e-13), written to `path` as FP64 .npy."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    import phantoms as P
+    c = P.plain_ellipsoids(n=n, seed=0)
+    x, it, rr, st = O.solve_volume(c["volume"], c["code"], c["value"], BETA)
+    np.save(path, x)
+    with open(path + ".json", "w") as f:
+        json.dump({"iters": it, "rel_resid": rr, "status": st, "threads": threads}, f)
+
+
+class OracleCheck:
+    """The FP64 oracle's solution of the benchmark system, computed in a
+    spawned process on the host cores while the GPU runs (started before the
+    first GPU call); compared with the GPU result after the timed region."""
+
+    def __init__(self, n):
+        import multiprocessing as mp
+        import tempfile
+        self.dir = tempfile.mkdtemp(prefix="rw_oracle_")
+        self.path = os.path.join(self.dir, "x.npy")
+        self.threads = max(1, (os.cpu_count() or 2) - 2)   # two cores left to the GPU's host thread
+        self.t0 = time.perf_counter()
+        self.proc = mp.get_context("spawn").Process(target=_oracle_solve_child, args=(n, self.threads, self.path))
+        self.proc.start()
+
+    def result(self, x_gpu, timeout=1800):
+        self.proc.join(timeout)
+        wall = time.perf_counter() - self.t0
+        try:
+            if self.proc.is_alive() or self.proc.exitcode != 0:
+                if self.proc.is_alive():
+                    self.proc.terminate()
+                return {"max_abs_err": None, "why": f"oracle process failed (exit {self.proc.exitcode})"}
+            xo = np.load(self.path)
+            with open(self.path + ".json") as f:
+                info = json.load(f)
+            d = np.abs(x_gpu.astype(np.float64) - xo)
+            far = np.abs(xo - 0.5) > 1e-3
+            return {"max_abs_err": float(d.max()), "mean_abs_err": float(d.mean()),
+                    "label_mismatches_far_from_half": int(np.count_nonzero((x_gpu[far] > 0.5) != (xo[far] > 0.5))),
+                    "voxels_far_from_half": int(np.count_nonzero(far)),
+                    "oracle": f"FP64 Jacobi-PCG to 1e-13 ({info['iters']} iterations, rel. residual "
+                              f"{info['rel_resid']:.2e}, {info['threads']} threads, {wall:.0f} s wall)",
+                    "gpu_output": "the last timed step's x (FP32)"}
+        finally:
+            for f in (self.path, self.path + ".json"):
+                if os.path.exists(f):
+                    os.remove(f)
+            os.rmdir(self.dir)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -199,6 +277,9 @@ def run(args):
     import phantoms as P
     N = args.n or 256
     c = P.plain_ellipsoids(n=N, seed=0)
+    solo = ws == 1 and rank == 0
+    cpu_base = _cpu_baseline(c) if solo and not args.no_cpu_baseline else None
+    check = OracleCheck(N) if solo and not args.no_oracle_check else None
     vol = torch.from_numpy(c["volume"]).to(dev)
     code = torch.from_numpy(c["code"]).to(dev)
     val = torch.from_numpy(c["value"]).to(dev)
@@ -275,21 +356,97 @@ def run(args):
                        "sweeps_per_graph": stats[0]["iters_per_graph"],
                        "l2": "inputs larger than L2 (about 470 MB streamed per sweep), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_256.get(tile_name) if N == 256 else None,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, median over "
-                                           "the k_sweep5 launches of this tile in a launch list "
-                                           "(profiles/launches_plain256.md, k_sweep5_plain256.md)",
+                         "frac": achieved / peak, "traffic": _sweep_traffic(tile_name, N),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of this "
+                                           "tile on the 256^3 workload, taken on the current sweep sources "
+                                           "(null when they changed since)",
                          "kernel": "k_sweep5 (fused PCG sweep)", "peak_source": src,
                          "algorithmic_bytes_per_launch": alg, "basis": "27 B per free voxel per sweep",
                          "kernel_bytes_per_voxel": KERNEL_BYTES_PER_VOXEL, "launch_ms": t_launch_s * 1e3,
                          "sweeps_per_step": sweeps / args.steps, "work_sweeps_per_step": work_sweeps / args.steps},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
-    if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(c)
+    if cpu_base is not None:
+        line["cpu_baseline"] = cpu_base
+    if solo and not args.no_secondary and N == 256:
+        line["secondary"] = {"hierarchical_1024": _hier_secondary(rw, P, torch, dev, peak, src, args)}
+    if check is not None:
+        line["max_abs_err_vs_oracle"] = check.result(out.cpu().numpy())
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def _hier_secondary(rw, P, torch, dev, peak, src, args):
+    """The hierarchical workload beside the headline: the 1024^3 uint16 vessel
+    tree, brick 32, pruning hom + dt, bricks solved to 1e-10 (the tolerance
+    of the hierarchy parity tests); one step = a full top-down run.  Then its
+    own leaf level solved twice from the same parent levels: batched
+    mixed-precision launches (the default) and the plain per-brick FP64 solve
+    (one brick per launch), both to 1e-10."""
+    s, tol, n = 32, 1e-10, 1024
+    ph = P.vessel_tree(n=n, seed=0, device=dev)
+    xyz, val = _labels_np(ph)
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    del ph
+    torch.cuda.empty_cache()
+    tree = rw.Tree(pyr, rw.Opts(brick_size=s, beta=BETA, tol=tol))
+    for _ in range(3):
+        tree.run(xyz, val)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record()
+    for _ in range(steps):
+        stats.append(tree.run(xyz, val))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    vi = sum(st["voxel_iters"] for st in stats)
+    sweep_ms = sum(st["ms_sweeps"] for st in stats)
+    eff = SWEEP_BYTES_PER_VOXEL * vi / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+    K = pyr.levels - 1
+    leaf = {}
+    res = {}
+    for name, kw in (("batched_mixed", {}), ("per_brick_fp64", {"batch_bricks": 0, "precision": "fp64"})):
+        t = tree if not kw else rw.Tree(pyr, rw.Opts(brick_size=s, beta=BETA, tol=tol, **kw))
+        if kw:
+            for k in range(K):       # the same parent levels for both leaf solves
+                t.refine_level(k, xyz if k == 0 else None, val if k == 0 else None)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        st = t.refine_level(K)
+        eb.record()
+        torch.cuda.synchronize()
+        lms = ea.elapsed_time(eb)
+        res[name] = {"leaf_bricks_solved": st["bricks_solved"], "leaf_voxel_iters": st["voxel_iters"],
+                     "leaf_ms": lms, "voxel_iter_per_s": st["voxel_iters"] / (lms / 1e3) if lms > 0 else None,
+                     "max_rel_resid": st["rel_resid"], "not_converged": st["not_converged"]}
+        leaf[name] = torch.empty(tuple(reversed(pyr.dims[K])), dtype=torch.float32, device=dev)
+        t.read_level(K, out=leaf[name])
+        if kw:
+            t.free()
+    a, b = res["batched_mixed"]["voxel_iter_per_s"], res["per_brick_fp64"]["voxel_iter_per_s"]
+    diff = (leaf["batched_mixed"] - leaf["per_brick_fp64"]).abs()
+    res["speedup"] = (a / b) if a and b else None
+    res["max_abs_diff_leaf"] = float(diff.max())
+    res["voxels_diff_above_1e-4"] = int((diff > 1e-4).sum())
+    res["accuracy"] = "both solve every leaf brick to ||r|| <= 1e-10 ||b|| (FP64 true residual)"
+    tree.free()
+    pyr.free()
+    torch.cuda.empty_cache()
+    return {"workload": f"hierarchical random walker, {n}^3 uint16 vessel tree (phantoms.vessel_tree, seed 0, "
+                        f"200 segments), brick {s}, e 1.25, pruning hom+dt, tol {tol}",
+            "value": vi / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+            "bricks_solved_per_run": stats[0]["bricks_solved"], "bricks_pruned_per_run": stats[0]["bricks_pruned"],
+            "gpu_launches_per_run": stats[0]["launches"],
+            "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s",
+                         "frac": (eff / peak) if eff else None, "traffic": None, "peak_source": src,
+                         "kernel": "fused PCG sweeps over the brick batches (device time of the sweeps)",
+                         "basis": "27 B per free-voxel iteration"},
+            "leaf_batched_vs_per_brick_fp64": res}
 
 
 def _labels_np(ph):
@@ -547,6 +704,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the FP64 oracle solve of the benchmark system (max_abs_err_vs_oracle)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the hierarchical 1024^3 workload reported beside the headline")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", default="auto", help="sweep tile (default: autotuned)")
     ap.add_argument("--workload", default="plain", choices=["plain", "hier", "adjoint", "multiclass"],

@@ -62,14 +62,17 @@ RAGGED = [((37, 23, 19), 1), ((5, 70, 33), 2), ((1, 1, 50), 3), ((2, 3, 1), 4), 
 
 
 @pytest.mark.parametrize("shape,seed", RAGGED)
-@pytest.mark.parametrize("beta,bound", [(10.0, 1e-6), (25.0, TOL)])
-def test_ragged_random_parity(rw, shape, seed, beta, bound):
+@pytest.mark.parametrize("beta,bound,tol", [(10.0, 1e-6, 1e-10), (25.0, TOL, 1e-13)])
+def test_ragged_random_parity(rw, shape, seed, beta, bound, tol):
     # uniform noise: with beta = 10 every weight is >= exp(-10), so both FP64
-    # references are accurate far below 1e-6; with beta = 25 weights reach
-    # exp(-25) and the configs' 1e-4 bound applies
+    # references are accurate far below 1e-6.  With beta = 25 weights reach
+    # exp(-25) ~ 1e-11: a segment attached only through such an edge moves the
+    # residual by ~1e-11 x its error, so it is resolved only at a tolerance
+    # that shows it (the 1 x 1 x 50 chain at 1e-13, where its FP32 rounds
+    # stagnate and FP64 sweeps finish it); the configs' 1e-4 bound applies
     c = P.random_case(shape, seed=seed, seed_frac=0.05, beta=beta)
-    xo = _oracle(c, beta)
-    x, st = _solve(rw, c, beta=beta, tol=1e-10)
+    xo = _oracle(c, beta, tol=1e-14)
+    x, st = _solve(rw, c, beta=beta, tol=tol)
     assert np.max(np.abs(x - xo)) <= bound
     assert _labels_agree(x, xo)
 
