@@ -201,7 +201,8 @@ class OracleCheck:
         self.path = os.path.join(self.dir, "x.npy")
         self.threads = max(1, (os.cpu_count() or 2) - 2)   # two cores left to the GPU's host thread
         self.t0 = time.perf_counter()
-        self.proc = mp.get_context("spawn").Process(target=_oracle_solve_child, args=(n, self.threads, self.path))
+        self.proc = mp.get_context("spawn").Process(target=_oracle_solve_child, args=(n, self.threads, self.path),
+                                                    daemon=True)
         self.proc.start()
 
     def result(self, x_gpu, timeout=1800):
@@ -411,9 +412,8 @@ def _hier_secondary(rw, P, torch, dev, peak, src, args):
     res = {}
     for name, kw in (("batched_mixed", {}), ("per_brick_fp64", {"batch_bricks": 0, "precision": "fp64"})):
         t = tree if not kw else rw.Tree(pyr, rw.Opts(brick_size=s, beta=BETA, tol=tol, **kw))
-        if kw:
-            for k in range(K):       # the same parent levels for both leaf solves
-                t.refine_level(k, xyz if k == 0 else None, val if k == 0 else None)
+        for k in range(K):       # the parent levels (the batched solve's) before the timed leaf level
+            t.refine_level(k, xyz if k == 0 else None, val if k == 0 else None)
         torch.cuda.synchronize()
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record()

@@ -338,6 +338,51 @@ rw_status rw_tree_read_level(const rw_tree* tree, int32_t level, const int64_t b
  * flags, brick minimum, maximum and max |new - old| (incremental pass). */
 rw_status rw_tree_node_stats(const rw_tree* tree, int32_t level, int64_t* n_nodes, int32_t* flags,
                              float* mn, float* mx, float* maxdiff);
+/* Level sharding over several GPUs (Sec. IV-D3: the nodes of a level are
+ * independent problems).  Each rank holds the pyramid and its own tree; a
+ * level is refined in parts instead of by rw_refine_level:
+ *   1. rw_tree_level_nodes lists the nodes the level solves in this pass
+ *      (identical on every rank, since every rank finished the same parent
+ *      level);
+ *   2. rw_refine_level_nodes solves a subset of them (a rank's share, e.g. a
+ *      contiguous range in Morton order); it opens the level, and may be
+ *      called again for further subsets;
+ *   3. rw_tree_export_nodes / rw_tree_import_nodes move solved nodes between
+ *      trees (values, flags and min / max / max-diff statistics);
+ *   4. rw_refine_level_finish, once every node of the level is present,
+ *      evaluates the level as rw_refine_level does after its solve: the fill
+ *      of absent nodes and the next level's node list.
+ * Full refinements only (not incremental passes).  While a level is open,
+ * rw_refine_level and rw_update_seeds on that tree return RW_ERR_INVALID_ARG.
+ * Node ids are brick indices of the level, (bz * nby + by) * nbx + bx. */
+
+/* The nodes `level` solves in this pass, ascending (pass nodes = NULL to
+ * query *n_nodes).  `level` must be 0 (a new pass), the next level of the
+ * pass, or the open level.  HOST arrays. */
+rw_status rw_tree_level_nodes(const rw_tree* tree, int32_t level, int64_t* n_nodes, int64_t* nodes);
+/* Solve the listed nodes of `level` (HOST array of n_nodes ids, each a node
+ * of the level not yet present; n_nodes may be 0).  `labels` as in
+ * rw_refine_level, at level 0 only.  stats.bricks_solved counts these
+ * nodes. */
+rw_status rw_refine_level_nodes(rw_tree* tree, int32_t level, const rw_labels* labels, const int64_t* nodes,
+                                int64_t n_nodes, rw_stats* stats, void* stream);
+/* Copy present nodes of the open level out: flags (RW_NODE_*, n_nodes
+ * int32), node_stats (n_nodes x {min, max, max |new - old|} float32) and
+ * values (n_nodes x s^3 float32, each brick x fastest; the voxels of a border
+ * brick outside the level are 0).  Each output is nullable; nodes, flags and
+ * node_stats are HOST arrays, values host or device memory. */
+rw_status rw_tree_export_nodes(const rw_tree* tree, int32_t level, const int64_t* nodes, int64_t n_nodes,
+                               int32_t* flags, float* node_stats, float* values, void* stream);
+/* Write nodes of the open level that another tree solved (arrays as
+ * exported; values host or device memory).  Each node must be a node of the
+ * level not yet present here, its flags must carry RW_NODE_SOLVED. */
+rw_status rw_tree_import_nodes(rw_tree* tree, int32_t level, const int64_t* nodes, int64_t n_nodes,
+                               const int32_t* flags, const float* node_stats, const float* values, void* stream);
+/* Close the open level once all its nodes are present (RW_ERR_INVALID_ARG
+ * otherwise): node status, the fill of absent nodes from the parent level and
+ * the next level's node list; stats count pruned nodes. */
+rw_status rw_refine_level_finish(rw_tree* tree, int32_t level, rw_stats* stats, void* stream);
+
 void rw_tree_free(rw_tree* tree);
 
 #ifdef __cplusplus

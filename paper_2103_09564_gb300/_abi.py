@@ -31,7 +31,8 @@ EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspa
            "rw_solve_adjoint",
            "rw_build_pyramid", "rw_build_pyramid_ex", "rw_pyramid_info", "rw_pyramid_read_level", "rw_pyramid_free", "rw_tree_create",
            "rw_refine_level", "rw_update_seeds", "rw_tree_read_level", "rw_tree_node_stats", "rw_tree_free",
-           "rw_trees_argmax", "rw_trees_argmax_changed", "rw_update_seeds_trees"]
+           "rw_trees_argmax", "rw_trees_argmax_changed", "rw_update_seeds_trees", "rw_tree_level_nodes",
+           "rw_refine_level_nodes", "rw_tree_export_nodes", "rw_tree_import_nodes", "rw_refine_level_finish"]
 
 
 class rw_volume(ctypes.Structure):
@@ -99,6 +100,12 @@ PROTOTYPES = {
     "rw_tree_read_level": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "rw_tree_node_stats": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "rw_tree_free": (None, [_P]),
+    "rw_tree_level_nodes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _P]),
+    "rw_refine_level_nodes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rw_labels), _P, ctypes.c_int64,
+                                             ctypes.POINTER(rw_stats), _P]),
+    "rw_tree_export_nodes": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "rw_tree_import_nodes": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "rw_refine_level_finish": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rw_stats), _P]),
 }
 
 _lib = None

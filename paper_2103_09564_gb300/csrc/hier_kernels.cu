@@ -509,4 +509,32 @@ cudaError_t launch_read_box(const float* field, int lx, int ly, int lz, const in
     return cudaGetLastError();
 }
 
+// Copy the bricks listed in `nodes` (brick indices, x fastest) between a
+// level field and a packed array [n][s][s][s] (x fastest within a brick):
+// to_packed = 1 exports (voxels of a truncated border brick outside the level
+// are written as 0), 0 imports (only voxels inside the level are written).
+__global__ void k_brick_io(float* field, int lx, int ly, int lz, int s, int nbx, int nby, const int64_t* nodes,
+                           int64_t n, float* packed, int to_packed) {
+    const int64_t per = (int64_t)s * s * s;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * per) return;
+    const int64_t i = k / per, r = k - i * per;
+    const int64_t b = nodes[i];
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
+    const int x = bx * s + (int)(r % s), y = by * s + (int)((r / s) % s), z = bz * s + (int)(r / ((int64_t)s * s));
+    const bool in = x < lx && y < ly && z < lz;
+    const int64_t f = ((int64_t)z * ly + y) * lx + x;
+    if (to_packed) packed[k] = in ? field[f] : 0.0f;
+    else if (in) field[f] = packed[k];
+}
+
+cudaError_t launch_brick_io(float* field, int lx, int ly, int lz, int s, int nbx, int nby, const int64_t* nodes,
+                            int64_t n, float* packed, int to_packed, cudaStream_t st) {
+    const int64_t tot = n * (int64_t)s * s * s;
+    if (tot <= 0) return cudaSuccess;
+    k_brick_io<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(field, lx, ly, lz, s, nbx, nby, nodes, n, packed,
+                                                               to_packed);
+    return cudaGetLastError();
+}
+
 }  // namespace rwk

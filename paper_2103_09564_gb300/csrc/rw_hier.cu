@@ -80,6 +80,13 @@ struct rw_tree {
     int refined = 0;         // levels of the current pass done
     int update = 0;          // current pass is incremental
     std::vector<std::array<int, 3>> resolve, reused;  // node lists for the next level
+    // a level refined in parts (rw_refine_level_nodes .. rw_refine_level_finish):
+    // its node lists and labels, and which of its nodes are present (solved
+    // here or imported)
+    int open_level = -1;
+    std::vector<std::array<int, 3>> open_nodes, open_reuse;
+    std::vector<rwk::LabelVox> open_labs;
+    std::vector<uint8_t> open_have;
 };
 
 namespace {
@@ -529,7 +536,8 @@ rw_status update_trees(rw_tree* const* trees, int n, const rw_labels* added, rw_
     for (int i = 0; i < n; ++i) {
         rw_tree* t = trees[i];
         if (!t) return fail(RW_ERR_INVALID_ARG, "tree %d is NULL", i);
-        if (t->refined != t->pyr->K + 1) return fail(RW_ERR_INVALID_ARG, "tree %d is not fully refined", i);
+        if (t->refined != t->pyr->K + 1 || t->open_level >= 0)
+            return fail(RW_ERR_INVALID_ARG, "tree %d is not fully refined", i);
         if (t->pyr != trees[0]->pyr) return fail(RW_ERR_INVALID_ARG, "trees on different pyramids");
         if (!same_solver_opts(t->opts, trees[0]->opts)) return fail(RW_ERR_INVALID_ARG, "trees with different options");
         for (int j = 0; j < i; ++j)
@@ -583,6 +591,62 @@ rw_status copy_labels(rw_tree* t, const rw_labels* lab, int added) {
         t->lab_val.push_back(lab->value[i]);
         t->lab_added.push_back((uint8_t)added);
         t->lab_cls.push_back(lab->cls ? lab->cls[i] : -1);
+    }
+    return RW_OK;
+}
+
+// A level refined in parts: start the pass at level 0 (labels stored as by
+// rw_refine_level), open the level's node lists.
+rw_status open_parts(rw_tree* t, int k, const rw_labels* labels) {
+    if (k < 0 || k > t->pyr->K) return fail(RW_ERR_INVALID_ARG, "level %d out of range", k);
+    if (t->open_level == k) return RW_OK;
+    if (t->open_level >= 0) return fail(RW_ERR_INVALID_ARG, "level %d is open", t->open_level);
+    if (k != 0 && k != t->refined) return fail(RW_ERR_INVALID_ARG, "levels must be refined in order");
+    if (k == 0) {
+        if (labels) {
+            t->lab_xyz.clear();
+            t->lab_val.clear();
+            t->lab_added.clear();
+            t->lab_cls.clear();
+            RCK(copy_labels(t, labels, 0));
+        }
+        t->update = 0;
+        t->refined = 0;
+        t->resolve.clear();
+        t->reused.clear();
+    }
+    LevelWork lw;
+    level_begin(t, k, &lw);
+    t->open_level = k;
+    t->open_nodes = lw.nodes;
+    t->open_reuse = lw.reuse;
+    t->open_labs = lw.labs;
+    t->open_have.assign(lw.nodes.size(), 0);
+    return RW_OK;
+}
+
+// Positions of `n` brick indices in the open level's node list; `want_have`:
+// every node must (1) or must not (0) be present already.
+rw_status open_positions(const rw_tree* t, int k, const int64_t* nodes, int64_t n, int want_have,
+                         std::vector<int64_t>* pos) {
+    if (t->open_level != k) return fail(RW_ERR_INVALID_ARG, "level %d is not open", k);
+    if (n < 0 || (n > 0 && !nodes)) return fail(RW_ERR_INVALID_ARG, "bad node list");
+    const TreeLevel& L = t->L[k];
+    std::unordered_map<int64_t, int64_t> at;
+    for (size_t i = 0; i < t->open_nodes.size(); ++i) at[brick_index(L, t->open_nodes[i])] = (int64_t)i;
+    pos->resize(n);
+    std::vector<uint8_t> seen(t->open_nodes.size(), 0);
+    for (int64_t i = 0; i < n; ++i) {
+        auto it = at.find(nodes[i]);
+        if (it == at.end()) return fail(RW_ERR_INVALID_ARG, "node %lld is not a node of level %d in this pass",
+                                        (long long)nodes[i], k);
+        if (seen[it->second]) return fail(RW_ERR_INVALID_ARG, "node %lld listed twice", (long long)nodes[i]);
+        seen[it->second] = 1;
+        if ((int)t->open_have[it->second] != want_have)
+            return fail(RW_ERR_INVALID_ARG, want_have ? "node %lld is not present in this tree"
+                                                      : "node %lld is already present in this tree",
+                        (long long)nodes[i]);
+        (*pos)[i] = it->second;
     }
     return RW_OK;
 }
@@ -735,6 +799,7 @@ rw_status rw_refine_level(rw_tree* t, int32_t level, const rw_labels* labels, rw
     if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
     if (level < 0 || level > t->pyr->K) return fail(RW_ERR_INVALID_ARG, "level %d out of range", level);
     if (level != 0 && level != t->refined) return fail(RW_ERR_INVALID_ARG, "levels must be refined in order");
+    if (t->open_level >= 0) return fail(RW_ERR_INVALID_ARG, "level %d is open (rw_refine_level_finish)", t->open_level);
     if (stats) memset(stats, 0, sizeof(*stats));
     if (level == 0) {
         if (labels) {
@@ -899,6 +964,168 @@ rw_status rw_tree_node_stats(const rw_tree* t, int32_t level, int64_t* n_nodes, 
     if (mn) memcpy(mn, L.mn.data(), L.nb * sizeof(float));
     if (mx) memcpy(mx, L.mx.data(), L.nb * sizeof(float));
     if (maxdiff) memcpy(maxdiff, L.md.data(), L.nb * sizeof(float));
+    return RW_OK;
+}
+
+rw_status rw_tree_level_nodes(const rw_tree* t, int32_t level, int64_t* n_nodes, int64_t* nodes) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!t || !n_nodes) return fail(RW_ERR_INVALID_ARG, "NULL argument");
+    if (level < 0 || level > t->pyr->K) return fail(RW_ERR_INVALID_ARG, "level %d out of range", level);
+    std::vector<int64_t> ids;
+    if (t->open_level == level) {
+        for (const auto& b : t->open_nodes) ids.push_back(brick_index(t->L[level], b));
+    } else if (level == 0) {
+        if (t->open_level >= 0) return fail(RW_ERR_INVALID_ARG, "level %d is open", t->open_level);
+        ids.push_back(0);
+    } else {
+        if (t->open_level >= 0 || level != t->refined)
+            return fail(RW_ERR_INVALID_ARG, "level %d is not the next level of the pass", level);
+        for (const auto& b : t->resolve) ids.push_back(brick_index(t->L[level], b));
+    }
+    std::sort(ids.begin(), ids.end());
+    if (nodes) std::copy(ids.begin(), ids.end(), nodes);
+    *n_nodes = (int64_t)ids.size();
+    return RW_OK;
+}
+
+rw_status rw_refine_level_nodes(rw_tree* t, int32_t level, const rw_labels* labels, const int64_t* nodes,
+                                int64_t n_nodes, rw_stats* stats, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_launches = 0;
+    const double t0 = now_ms();
+    if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (labels && level != 0) return fail(RW_ERR_INVALID_ARG, "labels are given at level 0");
+    RCK(check_labels(labels));
+    RCK(open_parts(t, level, labels));
+    std::vector<int64_t> pos;
+    RCK(open_positions(t, level, nodes, n_nodes, 0, &pos));
+    std::vector<std::array<int, 3>> sub;
+    for (int64_t i : pos) sub.push_back(t->open_nodes[i]);
+    std::sort(sub.begin(), sub.end());
+    if (stats) stats->bricks_active = (int64_t)sub.size();
+    if (!sub.empty()) {
+        DevWorkspace* w = nullptr;
+        RCK(enter(&w, stream));
+        LabelVox* dlab = nullptr;
+        const size_t nl = t->open_labs.size();
+        RCK(ws_get_t(w, S_LAB, std::max<size_t>(1, nl) * sizeof(LabelVox), &dlab));
+        if (nl) CK(cudaMemcpyAsync(dlab, t->open_labs.data(), nl * sizeof(LabelVox), cudaMemcpyHostToDevice, w->stream));
+        std::vector<Segment> segs = {{t, &sub, dlab, (int)nl}};
+        RCK(solve_segments(w, level, segs, stats));
+        RCK(leave(w));
+    }
+    for (int64_t i : pos) t->open_have[i] = 1;
+    if (stats) {
+        stats->ms = now_ms() - t0;
+        stats->launches = g_launches;
+    }
+    return RW_OK;
+}
+
+rw_status rw_tree_export_nodes(const rw_tree* t, int32_t level, const int64_t* nodes, int64_t n_nodes, int32_t* flags,
+                               float* node_stats, float* values, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
+    std::vector<int64_t> pos;
+    RCK(open_positions(t, level, nodes, n_nodes, 1, &pos));
+    const TreeLevel& L = t->L[level];
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        const int64_t bi = nodes[i];
+        if (flags) flags[i] = L.flags[bi];
+        if (node_stats) {
+            node_stats[3 * i] = L.mn[bi];
+            node_stats[3 * i + 1] = L.mx[bi];
+            node_stats[3 * i + 2] = L.md[bi];
+        }
+    }
+    if (!values || n_nodes == 0) return RW_OK;
+    const int s = t->pyr->s;
+    const auto& d = t->pyr->dims[level];
+    const int64_t nval = n_nodes * (int64_t)s * s * s;
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    int64_t* dn = nullptr;
+    RCK(ws_get_t(w, S_SHARD_N, n_nodes * sizeof(int64_t), &dn));
+    CK(cudaMemcpyAsync(dn, nodes, n_nodes * sizeof(int64_t), cudaMemcpyHostToDevice, w->stream));
+    const bool dev = is_device_ptr(values);
+    float* dst = values;
+    if (!dev) RCK(ws_get_t(w, S_SHARD_V, nval * 4, &dst));
+    CK(counted(launch_brick_io(L.P, d[0], d[1], d[2], s, L.nbx, L.nby, dn, n_nodes, dst, 1, w->stream)));
+    if (!dev) CK(cudaMemcpyAsync(values, dst, nval * 4, cudaMemcpyDeviceToHost, w->stream));
+    return leave(w);
+}
+
+rw_status rw_tree_import_nodes(rw_tree* t, int32_t level, const int64_t* nodes, int64_t n_nodes, const int32_t* flags,
+                               const float* node_stats, const float* values, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
+    if (n_nodes > 0 && (!flags || !node_stats || !values))
+        return fail(RW_ERR_INVALID_ARG, "flags, node statistics and values are required");
+    std::vector<int64_t> pos;
+    RCK(open_positions(t, level, nodes, n_nodes, 0, &pos));
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (!(flags[i] & RW_NODE_SOLVED)) return fail(RW_ERR_INVALID_ARG, "imported node %lld was not solved",
+                                                      (long long)nodes[i]);
+    if (n_nodes == 0) return RW_OK;
+    TreeLevel& L = t->L[level];
+    const int s = t->pyr->s;
+    const auto& d = t->pyr->dims[level];
+    const int64_t nval = n_nodes * (int64_t)s * s * s;
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    int64_t* dn = nullptr;
+    RCK(ws_get_t(w, S_SHARD_N, n_nodes * sizeof(int64_t), &dn));
+    CK(cudaMemcpyAsync(dn, nodes, n_nodes * sizeof(int64_t), cudaMemcpyHostToDevice, w->stream));
+    const float* src = values;
+    if (!is_device_ptr(values)) {
+        float* st = nullptr;
+        RCK(ws_get_t(w, S_SHARD_V, nval * 4, &st));
+        CK(cudaMemcpyAsync(st, values, nval * 4, cudaMemcpyHostToDevice, w->stream));
+        src = st;
+    }
+    CK(counted(launch_brick_io(L.P, d[0], d[1], d[2], s, L.nbx, L.nby, dn, n_nodes, const_cast<float*>(src), 0,
+                               w->stream)));
+    RCK(leave(w));
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        const int64_t bi = nodes[i];
+        L.flags[bi] = flags[i];
+        L.mn[bi] = node_stats[3 * i];
+        L.mx[bi] = node_stats[3 * i + 1];
+        L.md[bi] = node_stats[3 * i + 2];
+        t->open_have[pos[i]] = 1;
+    }
+    return RW_OK;
+}
+
+rw_status rw_refine_level_finish(rw_tree* t, int32_t level, rw_stats* stats, void* stream) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_launches = 0;
+    const double t0 = now_ms();
+    if (!t) return fail(RW_ERR_INVALID_ARG, "tree is NULL");
+    if (t->open_level != level) return fail(RW_ERR_INVALID_ARG, "level %d is not open", level);
+    for (size_t i = 0; i < t->open_have.size(); ++i)
+        if (!t->open_have[i])
+            return fail(RW_ERR_INVALID_ARG, "node %lld of level %d is neither solved nor imported",
+                        (long long)brick_index(t->L[level], t->open_nodes[i]), level);
+    if (stats) memset(stats, 0, sizeof(*stats));
+    LevelWork lw;
+    lw.nodes = t->open_nodes;
+    lw.reuse = t->open_reuse;
+    DevWorkspace* w = nullptr;
+    RCK(enter(&w, stream));
+    RCK(level_end(t, level, lw, stats, w));
+    RCK(leave(w));
+    t->refined = level + 1;
+    t->open_level = -1;
+    t->open_nodes.clear();
+    t->open_reuse.clear();
+    t->open_labs.clear();
+    t->open_have.clear();
+    if (stats) {
+        stats->ms = now_ms() - t0;
+        stats->launches = g_launches;
+    }
     return RW_OK;
 }
 

@@ -52,7 +52,7 @@ inline cudaError_t counted(cudaError_t e) {
 enum Slot {
     S_G, S_U0, S_U1, S_P0, S_P1, S_DELTA, S_XHI, S_PART, S_RPART, S_SC, S_NACT, S_VOL, S_CODE, S_VAL, S_X0, S_OUT,
     S_RHS, S_EXT, S_JOBS, S_LAB, S_BFLAGS, S_STATS, S_POOL_G, S_POOL_CODE, S_POOL_X, S_ADJ_PART, S_DBETA, S_DG,
-    S_XF, S_STATUS, S_GC, S_LIST, S_W64, S_NODES, S_COUNT
+    S_XF, S_STATUS, S_GC, S_LIST, S_W64, S_NODES, S_SHARD_V, S_SHARD_N, S_COUNT
 };
 
 struct DevWorkspace {

@@ -271,6 +271,8 @@ cudaError_t launch_argmax_nodes(const ClassFields& f, int lx, int ly, int lz, in
                                 const int64_t* nodes, int64_t n_nodes, uint8_t* labels, float* prob, cudaStream_t st);
 cudaError_t launch_argmax(const ClassFields& f, int lx, int ly, const int64_t box[6], uint8_t* labels, float* prob,
                           cudaStream_t s);
+cudaError_t launch_brick_io(float* field, int lx, int ly, int lz, int s, int nbx, int nby, const int64_t* nodes,
+                            int64_t n, float* packed, int to_packed, cudaStream_t st);
 cudaError_t launch_read_box(const float* field, int lx, int ly, int lz, const int64_t box[6], float* out,
                             cudaStream_t s);
 

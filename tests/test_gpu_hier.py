@@ -592,3 +592,62 @@ def test_multiclass_incremental_256_matches_oracle(rw):
         assert clear.mean() > 0.9
         got = labels.cpu().numpy()
         assert np.array_equal(got[clear], np.argmax(of, axis=0)[clear])
+
+
+def test_level_sharding_two_trees_match_oracle_and_unsharded(rw):
+    """Level sharding through the library on one GPU: two trees on one
+    pyramid stand for two ranks (no collective: their exports are imported
+    directly; level 2's values move through device memory).  Each level's
+    nodes are split into two Morton ranges, each tree solves its range,
+    imports the other's nodes and closes the level.  Both trees end up with
+    the same fields and node records, which match the oracle's H_p level by
+    level and an unsharded tree within the parity tolerance."""
+    import torch
+    from paper_2103_09564_gb300 import shard
+    ph = P.vessel_tree(n=96, seed=3, n_segments=30)
+    xyz, val = ph["labels_xyz"], ph["labels_value"]
+    s = 16
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True)
+    opts = rw.Opts(brick_size=s, beta=130.0, tol=HIER_TOL)
+    trees = [rw.Tree(pyr, opts) for _ in range(2)]
+    sh = [shard.TreeShard(t) for t in trees]
+    split = []
+    for k in range(pyr.levels):
+        ids = sh[0].level_nodes(k)
+        assert np.array_equal(ids, sh[1].level_nodes(k))
+        nbx, nby = sh[0].brick_grid(k)
+        parts = shard.partition(ids, nbx, nby, 2)
+        split.append([len(p) for p in parts])
+        for r in range(2):
+            sh[r].solve(k, parts[r], (xyz, val) if k == 0 else None)
+        if k == 2:
+            ex = [sh[r].export(k, parts[r], torch.empty((len(parts[r]), s ** 3), device="cuda")) for r in range(2)]
+        else:
+            ex = [sh[r].export(k, parts[r]) for r in range(2)]
+        if k == 1:
+            with pytest.raises(rw.RWError):        # the level is incomplete
+                sh[0].finish(k)
+            with pytest.raises(rw.RWError):        # a level is open
+                trees[0].refine_level(k)
+        sh[0].import_(k, ex[1])
+        sh[1].import_(k, ex[0])
+        if k == 1 and len(parts[0]):
+            with pytest.raises(rw.RWError):        # already present
+                sh[1].import_(k, ex[0])
+        for r in range(2):
+            sh[r].finish(k)
+    assert any(min(a, b) > 0 for a, b in split)
+    for k in range(pyr.levels):
+        assert np.array_equal(trees[0].read_level(k), trees[1].read_level(k)), k
+        for a, b in zip(trees[0].node_stats(k), trees[1].node_stats(k)):
+            assert np.array_equal(a, b), k
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), s)
+    oo = hrw.Opts(brick_size=s, beta=130.0)
+    ot = hrw.run(levels, xyz, val, oo)
+    _compare(rw, trees[0], ot, oo, s)
+    whole = rw.Tree(pyr, opts)
+    whole.run(xyz, val)
+    det = determined_mask(levels[-1], 130.0)
+    diff = np.abs(whole.read_level(pyr.levels - 1) - trees[0].read_level(pyr.levels - 1))
+    assert np.max(diff[det]) <= TOL
