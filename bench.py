@@ -467,10 +467,20 @@ def run_hier(args):
     dev = torch.device("cuda", 0)
     ph = P.vessel_tree(n=n, seed=0, device=dev)
     xyz, val = _labels_np(ph)
-    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=args.leaf_host)
-    del ph
+    torch.cuda.synchronize()
+    rw.release_workspace()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=args.leaf_host,
+                              all_in_host=args.all_host)
     opts = rw.Opts(brick_size=s, beta=BETA, tol=args.tol)
     tree = rw.Tree(pyr, opts)
+    rw.release_workspace()
+    dev_bytes = free0 - torch.cuda.mem_get_info(dev)[0]     # what the pyramid and the tree hold in HBM
+    level_vox = [x * y * z for x, y, z in pyr.dims]
+    held = {"pyramid_bytes": 2 * level_vox[-1] + 4 * sum(level_vox[:-1]), "tree_field_bytes": 4 * sum(level_vox),
+            "device_bytes_of_pyramid_and_tree": int(dev_bytes)}
+    del ph
+    torch.cuda.empty_cache()
     for _ in range(max(3, args.warmup)):
         tree.run(xyz, val)
     torch.cuda.synchronize()
@@ -500,7 +510,9 @@ def run_hier(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"hierarchical random walker, {n}^3 uint16 vessel tree (phantoms.vessel_tree, "
                                    f"seed 0, 200 segments), brick {s}, e 1.25, pruning hom+dt, tol {args.tol}"
-                                   + (", leaf level in host memory" if args.leaf_host else ""),
+                                   + (", leaf level in host memory" if args.leaf_host else "")
+                                   + (", every level in host memory" if args.all_host else ""),
+                       "memory": held,
                        "levels": per_level, "bricks_solved_per_run": stats[0]["bricks_solved"],
                        "bricks_pruned_per_run": stats[0]["bricks_pruned"], "labels": int(len(val))},
             "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s",
@@ -719,6 +731,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=0, help="bricks per batched solve (0: library default)")
     ap.add_argument("--leaf-host", action="store_true",
                     help="hier: leaf level in mapped host memory (out-of-core placement)")
+    ap.add_argument("--all-host", action="store_true",
+                    help="hier: every pyramid level and tree field in mapped host memory (out-of-core placement)")
     ap.add_argument("--n", type=int, default=0,
                     help="volume edge (default: 256 plain, 1024 hier, 96 adjoint; smaller for profiling)")
     args = ap.parse_args()

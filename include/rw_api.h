@@ -156,7 +156,10 @@ enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, 
        RW_TILE_T32x20 = 26, RW_TILE_T64x11 = 27, RW_TILE_T32x12 = 28, RW_TILE_T40x20 = 29, RW_TILE_T40x8 = 30,
        /* strips of 4 with 3 planes in flight (_D3) or 1 (_D1; s64x14_d1: 320 threads) */
        RW_TILE_S32x20_D3 = 31, RW_TILE_S64x8_D3 = 32, RW_TILE_S32x22_D1 = 33, RW_TILE_S64x8_D1 = 34,
-       RW_TILE_S64x14_D1 = 35 };
+       RW_TILE_S64x14_D1 = 35,
+       /* strips of 4 whose p_k and u' are exchanged through the load ring (_D: planes ahead) */
+       RW_TILE_R64x14_D2 = 36, RW_TILE_R64x14_D1 = 37, RW_TILE_R64x11_D2 = 38, RW_TILE_R64x11_D3 = 39,
+       RW_TILE_R32x22_D2 = 40, RW_TILE_R32x20_D3 = 41 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */
@@ -248,10 +251,15 @@ rw_status rw_solve_adjoint(const rw_volume* vol, const rw_seed_mask* seeds, cons
  * with ceil-halved dims, until every dim is <= brick_size (the root). */
 rw_status rw_build_pyramid(const rw_volume* vol, int32_t brick_size, rw_pyramid** out, void* stream);
 
-/* Placement of a tree's leaf-level field (rw_opts.leaf_field):
- * RW_LEAF_AS_PYRAMID: host memory when the pyramid's leaf is (RW_PYR_LEAF_HOST),
- * else HBM; RW_LEAF_HBM / RW_LEAF_HOST: HBM / pinned, mapped host memory. */
-typedef enum rw_leaf_field { RW_LEAF_AS_PYRAMID = 0, RW_LEAF_HBM = 1, RW_LEAF_HOST = 2 } rw_leaf_field;
+/* Placement of a tree's level fields (rw_opts.leaf_field):
+ * RW_LEAF_AS_PYRAMID: as the pyramid's levels (RW_PYR_HOST_ALL: every level's
+ * field in host memory; RW_PYR_LEAF_HOST: the leaf field in host memory;
+ * otherwise HBM); RW_LEAF_HBM / RW_LEAF_HOST: the leaf field in HBM / in
+ * pinned, mapped host memory (coarser fields in HBM); RW_FIELDS_HOST: every
+ * level's field in pinned, mapped host memory. */
+typedef enum rw_leaf_field {
+    RW_LEAF_AS_PYRAMID = 0, RW_LEAF_HBM = 1, RW_LEAF_HOST = 2, RW_FIELDS_HOST = 3
+} rw_leaf_field;
 
 /* rw_build_pyramid with placement flags.  RW_PYR_LEAF_HOST: the leaf level
  * (its unorm16 intensities here, and by default the leaf probability fields
@@ -262,6 +270,15 @@ typedef enum rw_leaf_field { RW_LEAF_AS_PYRAMID = 0, RW_LEAF_HBM = 1, RW_LEAF_HO
  * batches of one level occupy HBM.  Results are identical to the HBM
  * placement.  Unknown flag bits: RW_ERR_INVALID_ARG. */
 #define RW_PYR_LEAF_HOST 1
+/* RW_PYR_HOST_ALL: every level of the pyramid in pinned, mapped host memory,
+ * and by default every level's field of the trees built on it: HBM then holds
+ * only the working set of one batched level solve (the brick pool and solver
+ * vectors of at most rw_opts.max_batch bricks) and the library's workspace.
+ * A host input volume is normalised in z-slabs of at most 256 MB, so no
+ * device copy of the whole volume is made.  The paper streams bricks from
+ * disk (Sec. III-A, IV-A); here the backing store is the host memory the GPU
+ * reads and writes in place over the coherent host link. */
+#define RW_PYR_HOST_ALL 2
 rw_status rw_build_pyramid_ex(const rw_volume* vol, int32_t brick_size, int32_t flags, rw_pyramid** out,
                               void* stream);
 /* Number of levels and their dims (levels x 3, x/y/z; level 0 = root). */

@@ -56,7 +56,7 @@ def Opts(**kw) -> _abi.rw_opts:
     """rw_opts with the library defaults, overridden by keyword (precision may
     be 'mixed'/'fp64', tile a name such as '40x8', weight 'gaussian'/'poisson'
     -- for 'poisson', beta is the count that g = 1 stands for --, leaf_field
-    'pyramid'/'hbm'/'host')."""
+    'pyramid'/'hbm'/'host'/'host_all')."""
     o = _abi.rw_opts()
     load().rw_opts_default(ctypes.byref(o))
     for k, v in kw.items():
@@ -67,7 +67,8 @@ def Opts(**kw) -> _abi.rw_opts:
         if k == "weight" and isinstance(v, str):
             v = {"gaussian": 0, "poisson": 1}[v]
         if k == "leaf_field" and isinstance(v, str):
-            v = {"pyramid": _abi.RW_LEAF_AS_PYRAMID, "hbm": _abi.RW_LEAF_HBM, "host": _abi.RW_LEAF_HOST}[v]
+            v = {"pyramid": _abi.RW_LEAF_AS_PYRAMID, "hbm": _abi.RW_LEAF_HBM, "host": _abi.RW_LEAF_HOST,
+                 "host_all": _abi.RW_FIELDS_HOST}[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(o, k, v)
@@ -262,16 +263,19 @@ class Pyramid:
             pass
 
 
-RW_PYR_LEAF_HOST = 1
+RW_PYR_LEAF_HOST, RW_PYR_HOST_ALL = _abi.RW_PYR_LEAF_HOST, _abi.RW_PYR_HOST_ALL
 
 
-def rw_build_pyramid(volume, brick_size=32, *, lo=0.0, hi=1.0, normalize=False, leaf_in_host=False) -> Pyramid:
+def rw_build_pyramid(volume, brick_size=32, *, lo=0.0, hi=1.0, normalize=False, leaf_in_host=False,
+                     all_in_host=False) -> Pyramid:
     """leaf_in_host: keep the leaf level (and the leaf fields of trees built on
     this pyramid) in mapped host memory, read and written by the GPU in place
-    (out-of-core placement for volumes whose leaf does not fit in HBM)."""
+    (out-of-core placement for volumes whose leaf does not fit in HBM).
+    all_in_host: every level there, and every level's field of the trees built
+    on it: HBM holds only the working set of a batched level solve."""
     v, va, _ = _volume(volume, lo, hi, normalize, RW_STORE_UNORM16, False)
     h = ctypes.c_void_p(0)
-    flags = RW_PYR_LEAF_HOST if leaf_in_host else 0
+    flags = (RW_PYR_LEAF_HOST if leaf_in_host else 0) | (RW_PYR_HOST_ALL if all_in_host else 0)
     _check(load().rw_build_pyramid_ex(ctypes.byref(v), brick_size, flags, ctypes.byref(h), _stream(va)))
     return Pyramid(h.value)
 

@@ -14,7 +14,8 @@ STATUS_NAMES = ["RW_OK", "RW_ERR_INVALID_ARG", "RW_ERR_NO_SEEDS", "RW_ERR_NOT_CO
 RW_U16, RW_F32 = 0, 1
 RW_STORE_UNORM16, RW_STORE_F32 = 0, 1
 RW_MIXED, RW_FP64 = 0, 1
-RW_LEAF_AS_PYRAMID, RW_LEAF_HBM, RW_LEAF_HOST = 0, 1, 2
+RW_LEAF_AS_PYRAMID, RW_LEAF_HBM, RW_LEAF_HOST, RW_FIELDS_HOST = 0, 1, 2, 3
+RW_PYR_LEAF_HOST, RW_PYR_HOST_ALL = 1, 2
 RW_CODE_FREE, RW_CODE_SEED, RW_CODE_ABSENT = 0, 1, 2
 RW_NODE_SOLVED, RW_NODE_PRUNABLE, RW_NODE_HOM, RW_NODE_DT, RW_NODE_CFL, RW_NODE_SIMILAR, RW_NODE_REUSED, \
     RW_NODE_CFL_ADDED, RW_NODE_NO_SEEDS, RW_NODE_CHANGED = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
@@ -24,7 +25,8 @@ RW_TILE = {"auto": 0, "32x16": 1, "64x8": 2, "40x8": 3, "40x20": 4, "80x8": 5, "
            "64x16": 9, "w28x28": 10, "w28x12": 11, "w28x20": 12, "w28x28_8w": 13, "p32x12": 14, "p32x12_deep": 15,
            "p32x28": 16, "p40x20": 17, "p40x8": 18, "p32x20": 19, "s64x11": 20, "s32x22": 21, "s32x20": 22,
            "s64x8": 23, "s40x20": 24, "s40x8": 25, "t32x20": 26, "t64x11": 27, "t32x12": 28, "t40x20": 29,
-           "t40x8": 30, "s32x20_d3": 31, "s64x8_d3": 32, "s32x22_d1": 33, "s64x8_d1": 34, "s64x14_d1": 35}
+           "t40x8": 30, "s32x20_d3": 31, "s64x8_d3": 32, "s32x22_d1": 33, "s64x8_d1": 34, "s64x14_d1": 35,
+           "r64x14_d2": 36, "r64x14_d1": 37, "r64x11_d2": 38, "r64x11_d3": 39, "r32x22_d2": 40, "r32x20_d3": 41}
 
 # every function declared in include/rw_api.h
 EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspace", "rw_solve", "rw_solve_noalloc",

@@ -139,7 +139,7 @@ rw_status check_opts(const rw_opts& o) {
         (o.precision != RW_MIXED && o.precision != RW_FP64) || o.iters_per_graph < 2 || o.tile < 0 || o.tile >= N_TILES ||
         o.brick_size < 2 || !(o.expand >= 1.0f) || o.max_batch < 1 ||
         (o.weight != RW_WEIGHT_GAUSSIAN && o.weight != RW_WEIGHT_POISSON) || o.leaf_field < RW_LEAF_AS_PYRAMID ||
-        o.leaf_field > RW_LEAF_HOST)
+        o.leaf_field > RW_FIELDS_HOST)
         return fail(RW_ERR_INVALID_ARG, "invalid rw_opts");
     return RW_OK;
 }
@@ -184,7 +184,8 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
         c = {TILE_S40x20, TILE_S40x8};
     } else {
         c = {TILE_S64x11,    TILE_S32x22,    TILE_S32x20,    TILE_S64x8,     TILE_S32x20_D3,
-             TILE_S64x8_D3,  TILE_S32x22_D1, TILE_S64x8_D1,  TILE_S64x14_D1};
+             TILE_S64x8_D3,  TILE_S32x22_D1, TILE_S64x8_D1,  TILE_S64x14_D1, TILE_R64x14_D2,
+             TILE_R64x14_D1, TILE_R64x11_D2, TILE_R64x11_D3, TILE_R32x22_D2, TILE_R32x20_D3};
     }
     std::vector<int> ok;
     for (int t : c)

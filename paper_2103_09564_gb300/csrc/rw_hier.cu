@@ -26,6 +26,8 @@ struct rw_pyramid {
     int device = 0;
     int leaf_host = 0;                       // leaf level in mapped host memory
     void* leaf_host_ptr = nullptr;           // its host allocation
+    int host_all = 0;                        // every level in mapped host memory
+    std::vector<void*> lv_host;              // host allocations of the coarse levels (host_all)
 };
 
 namespace {
@@ -663,7 +665,8 @@ rw_status rw_build_pyramid_ex(const rw_volume* vol, int32_t brick_size, int32_t 
                               void* stream) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     if (!out) return fail(RW_ERR_INVALID_ARG, "out is NULL");
-    if (flags & ~RW_PYR_LEAF_HOST) return fail(RW_ERR_INVALID_ARG, "unknown pyramid flags 0x%x", flags);
+    if (flags & ~(RW_PYR_LEAF_HOST | RW_PYR_HOST_ALL))
+        return fail(RW_ERR_INVALID_ARG, "unknown pyramid flags 0x%x", flags);
     *out = nullptr;
     int64_t nvox = 0, batch = 1;
     RCK(check_volume(vol, &nvox, &batch));
@@ -688,21 +691,44 @@ rw_status rw_build_pyramid_ex(const rw_volume* vol, int32_t brick_size, int32_t 
         rw_pyramid_free(py);
         return st;
     };
-    py->leaf_host = (flags & RW_PYR_LEAF_HOST) ? 1 : 0;
+    py->host_all = (flags & RW_PYR_HOST_ALL) ? 1 : 0;
+    py->leaf_host = (flags & (RW_PYR_LEAF_HOST | RW_PYR_HOST_ALL)) ? 1 : 0;
+    py->lv_host.assign(dims.size(), nullptr);
     void* leaf_dev = nullptr;
     cudaError_t e = level_alloc(py->leaf_host, nvox * 2, &leaf_dev, &py->leaf_host_ptr);
     py->leaf = static_cast<uint16_t*>(leaf_dev);
     if (e != cudaSuccess) return cleanup(fail(RW_ERR_OOM, "pyramid leaf: %s", cudaGetErrorString(e)));
     for (int k = 0; k < py->K; ++k) {
         const int64_t n = (int64_t)dims[k][0] * dims[k][1] * dims[k][2];
-        e = cudaMalloc(&py->lv[k], n * 4);
+        void* lv = nullptr;
+        e = level_alloc(py->host_all, n * 4, &lv, &py->lv_host[k]);
+        py->lv[k] = static_cast<float*>(lv);
         if (e != cudaSuccess) return cleanup(fail(RW_ERR_OOM, "pyramid level %d: %s", k, cudaGetErrorString(e)));
     }
-    const void* dvol = nullptr;
-    rw_status st = stage_in(w, S_VOL, vol->data, nvox * (vol->dtype == RW_U16 ? 2 : 4), &dvol);
-    if (st != RW_OK) return cleanup(st);
-    e = launch_quantize(dvol, vol->dtype, nvox, vol->lo, vol->hi, vol->normalize, RW_STORE_UNORM16, py->leaf,
-                        w->stream);
+    // the leaf: device input is quantised in place; host input is copied in
+    // z-slabs of at most 256 MB, so no device copy of the whole volume is made
+    const size_t esz = vol->dtype == RW_U16 ? 2 : 4;
+    if (is_device_ptr(vol->data)) {
+        e = launch_quantize(vol->data, vol->dtype, nvox, vol->lo, vol->hi, vol->normalize, RW_STORE_UNORM16, py->leaf,
+                            w->stream);
+    } else {
+        const int64_t plane = (int64_t)dd[0] * dd[1];
+        const auto& lf = dims[py->K];
+        const int64_t pl = (int64_t)lf[0] * lf[1];
+        const int64_t zs = std::max<int64_t>(1, ((int64_t)256 << 20) / (pl * (int64_t)esz));
+        (void)plane;
+        void* buf = nullptr;
+        rw_status st = ws_get(w, S_VOL, (size_t)std::min<int64_t>(zs, lf[2]) * pl * esz, &buf);
+        if (st != RW_OK) return cleanup(st);
+        for (int64_t z0 = 0; z0 < lf[2] && e == cudaSuccess; z0 += zs) {
+            const int64_t nz = std::min<int64_t>(zs, lf[2] - z0);
+            e = cudaMemcpyAsync(buf, static_cast<const char*>(vol->data) + z0 * pl * esz, nz * pl * esz,
+                                cudaMemcpyHostToDevice, w->stream);
+            if (e == cudaSuccess)
+                e = launch_quantize(buf, vol->dtype, nz * pl, vol->lo, vol->hi, vol->normalize, RW_STORE_UNORM16,
+                                    py->leaf + z0 * pl, w->stream);
+        }
+    }
     for (int k = py->K - 1; k >= 0 && e == cudaSuccess; --k) {
         const auto& f = dims[k + 1];
         if (k == py->K - 1) e = launch_downsample_u16(py->leaf, f[0], f[1], f[2], py->lv[k], w->stream);
@@ -743,8 +769,8 @@ rw_status rw_pyramid_read_level(const rw_pyramid* py, int32_t level, float* out,
 void rw_pyramid_free(rw_pyramid* py) {
     if (!py) return;
     level_free(py->leaf, py->leaf_host_ptr);
-    for (float* p : py->lv)
-        if (p) cudaFree(p);
+    for (size_t k = 0; k < py->lv.size(); ++k)
+        level_free(py->lv[k], k < py->lv_host.size() ? py->lv_host[k] : nullptr);
     delete py;
 }
 
@@ -769,8 +795,9 @@ rw_status rw_tree_create(const rw_pyramid* py, const rw_opts* opts_in, rw_tree**
         L.nbz = (d[2] + py->s - 1) / py->s;
         L.nb = (int64_t)L.nbx * L.nby * L.nbz;
         const int64_t n = (int64_t)d[0] * d[1] * d[2];
-        const bool host = k == py->K && (o.leaf_field == RW_LEAF_HOST ||
-                                         (o.leaf_field == RW_LEAF_AS_PYRAMID && py->leaf_host));
+        const bool all = o.leaf_field == RW_FIELDS_HOST || (o.leaf_field == RW_LEAF_AS_PYRAMID && py->host_all);
+        const bool host = all || (k == py->K && (o.leaf_field == RW_LEAF_HOST ||
+                                                 (o.leaf_field == RW_LEAF_AS_PYRAMID && py->leaf_host)));
         void* p0 = nullptr;
         cudaError_t e = level_alloc(host, n * 4, &p0, &L.P_host);
         L.P = static_cast<float*>(p0);

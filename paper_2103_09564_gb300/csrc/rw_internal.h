@@ -84,8 +84,11 @@ enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE
               TILE_P40x8 = 18, TILE_P32x20 = 19, TILE_S64x11 = 20, TILE_S32x22 = 21, TILE_S32x20 = 22,
               TILE_S64x8 = 23, TILE_S40x20 = 24, TILE_S40x8 = 25, TILE_T32x20 = 26, TILE_T64x11 = 27,
               TILE_T32x12 = 28, TILE_T40x20 = 29, TILE_T40x8 = 30, TILE_S32x20_D3 = 31, TILE_S64x8_D3 = 32,
-              TILE_S32x22_D1 = 33, TILE_S64x8_D1 = 34, TILE_S64x14_D1 = 35 };
-constexpr int N_TILES = 36;
+              TILE_S32x22_D1 = 33, TILE_S64x8_D1 = 34, TILE_S64x14_D1 = 35,
+              // strips of 4 whose p_k and u' are exchanged through the TMA ring slots
+              TILE_R64x14_D2 = 36, TILE_R64x14_D1 = 37, TILE_R64x11_D2 = 38, TILE_R64x11_D3 = 39, TILE_R32x22_D2 = 40, TILE_R32x20_D3 = 41 };
+constexpr int N_TILES = 42;
+constexpr int TILE_RING_FIRST = TILE_R64x14_D2;  // k_sweep5 with the ring exchange
 constexpr int TILE_PADDED_FIRST = TILE_P32x12;  // tiles from here on use the padded layout (k_sweep4)
 constexpr int TILE_STRIP_FIRST = TILE_S64x11;   // tiles from here on: k_sweep5 (strips of 4, then of 2)
 constexpr int TILE_STRIP2_FIRST = TILE_T32x20;  // k_sweep5 with 2-voxel strips

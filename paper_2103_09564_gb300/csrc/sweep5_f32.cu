@@ -5,41 +5,49 @@ namespace rwk {
 
 namespace {
 
-// tile id -> (TX, TY, voxels per strip, threads, planes ahead, minimum resident CTAs)
-#define RW_STRIP_TILES(X)         \
-    X(20, 64, 11, 4, 256, 2, 2)   \
-    X(21, 32, 22, 4, 256, 2, 2)   \
-    X(22, 32, 20, 4, 256, 2, 2)   \
-    X(23, 64, 8, 4, 224, 2, 2)    \
-    X(24, 40, 20, 4, 288, 2, 2)   \
-    X(25, 40, 8, 4, 160, 2, 3)    \
-    X(26, 32, 20, 2, 416, 2, 2)   \
-    X(27, 64, 11, 2, 480, 2, 2)   \
-    X(28, 32, 12, 2, 288, 2, 3)   \
-    X(29, 40, 20, 2, 512, 2, 2)   \
-    X(30, 40, 8, 2, 256, 2, 4)    \
-    X(31, 32, 20, 4, 256, 3, 2)   \
-    X(32, 64, 8, 4, 224, 3, 2)    \
-    X(33, 32, 22, 4, 256, 1, 2)   \
-    X(34, 64, 8, 4, 224, 1, 3)    \
-    X(35, 64, 14, 4, 320, 1, 2)
+// tile id -> (TX, TY, voxels per strip, threads, planes ahead, minimum resident
+// CTAs, p_k and u' exchanged through the ring slots)
+#define RW_STRIP_TILES(X)                \
+    X(20, 64, 11, 4, 256, 2, 2, false)   \
+    X(21, 32, 22, 4, 256, 2, 2, false)   \
+    X(22, 32, 20, 4, 256, 2, 2, false)   \
+    X(23, 64, 8, 4, 224, 2, 2, false)    \
+    X(24, 40, 20, 4, 288, 2, 2, false)   \
+    X(25, 40, 8, 4, 160, 2, 3, false)    \
+    X(26, 32, 20, 2, 416, 2, 2, false)   \
+    X(27, 64, 11, 2, 480, 2, 2, false)   \
+    X(28, 32, 12, 2, 288, 2, 3, false)   \
+    X(29, 40, 20, 2, 512, 2, 2, false)   \
+    X(30, 40, 8, 2, 256, 2, 4, false)    \
+    X(31, 32, 20, 4, 256, 3, 2, false)   \
+    X(32, 64, 8, 4, 224, 3, 2, false)    \
+    X(33, 32, 22, 4, 256, 1, 2, false)   \
+    X(34, 64, 8, 4, 224, 1, 3, false)    \
+    X(35, 64, 14, 4, 320, 1, 2, false)   \
+    X(36, 64, 14, 4, 320, 2, 2, true)    \
+    X(37, 64, 14, 4, 320, 1, 2, true)    \
+    X(38, 64, 11, 4, 256, 2, 2, true)    \
+    X(39, 64, 11, 4, 256, 3, 2, true)    \
+    X(40, 32, 22, 4, 256, 2, 2, true)    \
+    X(41, 32, 20, 4, 256, 3, 2, true)
 
-template <int TX, int TY, int V, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB, bool R>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
-    k_sweep5<TX, TY, V, NT, D, MB><<<grid, NT, sweep5_smem_bytes<TX, TY, V, D>(), s>>>(a);
+    k_sweep5<TX, TY, V, NT, D, MB, false, R><<<grid, NT, sweep5_smem_bytes<TX, TY, V, D, R>(), s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TX, int TY, int V, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB, bool R>
 cudaError_t prepare_one() {
-    return cudaFuncSetAttribute(k_sweep5<TX, TY, V, NT, D, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep5_smem_bytes<TX, TY, V, D>());
+    return cudaFuncSetAttribute(k_sweep5<TX, TY, V, NT, D, MB, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep5_smem_bytes<TX, TY, V, D, R>());
 }
 
-template <int TX, int TY, int V, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB, bool R>
 int occupancy_one() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, V, NT, D, MB>, NT, sweep5_smem_bytes<TX, TY, V, D>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, V, NT, D, MB, false, R>, NT,
+                                                  sweep5_smem_bytes<TX, TY, V, D, R>());
     return n;
 }
 
@@ -92,9 +100,9 @@ int sweep5_occupancy_loop(int tile) {
 
 cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     switch (tile) {
-#define X(id, tx, ty, v, nt, d, mb) \
-    case id:                        \
-        return launch_one<tx, ty, v, nt, d, mb>(a, grid, s);
+#define X(id, tx, ty, v, nt, d, mb, r) \
+    case id:                           \
+        return launch_one<tx, ty, v, nt, d, mb, r>(a, grid, s);
         RW_STRIP_TILES(X)
 #undef X
     default:
@@ -104,9 +112,9 @@ cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s
 
 cudaError_t sweep5_prepare(int tile) {
     switch (tile) {
-#define X(id, tx, ty, v, nt, d, mb) \
-    case id:                        \
-        return prepare_one<tx, ty, v, nt, d, mb>();
+#define X(id, tx, ty, v, nt, d, mb, r) \
+    case id:                           \
+        return prepare_one<tx, ty, v, nt, d, mb, r>();
         RW_STRIP_TILES(X)
 #undef X
     default:
@@ -116,9 +124,9 @@ cudaError_t sweep5_prepare(int tile) {
 
 int sweep5_occupancy(int tile) {
     switch (tile) {
-#define X(id, tx, ty, v, nt, d, mb) \
-    case id:                        \
-        return occupancy_one<tx, ty, v, nt, d, mb>();
+#define X(id, tx, ty, v, nt, d, mb, r) \
+    case id:                           \
+        return occupancy_one<tx, ty, v, nt, d, mb, r>();
         RW_STRIP_TILES(X)
 #undef X
     default:
@@ -128,9 +136,9 @@ int sweep5_occupancy(int tile) {
 
 size_t sweep5_smem(int tile) {
     switch (tile) {
-#define X(id, tx, ty, v, nt, d, mb) \
-    case id:                        \
-        return sweep5_smem_bytes<tx, ty, v, d>();
+#define X(id, tx, ty, v, nt, d, mb, r) \
+    case id:                           \
+        return sweep5_smem_bytes<tx, ty, v, d, r>();
         RW_STRIP_TILES(X)
 #undef X
     default:

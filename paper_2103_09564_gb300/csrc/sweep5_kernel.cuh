@@ -53,31 +53,39 @@
 
 namespace rwk {
 
-template <int TX, int TY, int V, int D>
+template <int TX, int TY, int V, int D, bool RING = false>
 struct Strip {
     static constexpr int SX = TX / V + 2;       // strips per row (one halo strip each side)
     static constexpr int RY = TY + 3;           // rows y = -1 .. TY+1
     static constexpr int WS = TX + 2 * V;       // words per row
     static constexpr int PL = RY * WS;          // words per plane
     static constexpr int PS = RY * SX;          // strips per plane
-    static constexpr int NR = D + 2;            // ring planes
+    static constexpr int NR = D + 2;            // ring planes of p, g, delta
+    // ring planes of u: with RING, u' replaces u in its slot and is read one
+    // step later (the delta of the plane behind), so the slot lives a step longer
+    static constexpr int NRU = RING ? D + 3 : D + 2;
     static constexpr int NI = TX * TY;          // interior voxels
     // delta box: the interior (V = 4: its first column is 16-byte aligned),
     // or the full strip width from the halo strip (V = 2)
     static constexpr int XW = V == 4 ? TX : WS, XC = V == 4 ? V : 0;
     static constexpr int PLA = (PL + 31) & ~31; // ring plane stride (128-byte aligned TMA destinations)
     static constexpr int NIA = (XW * TY + 31) & ~31;
-    // words: ring (u, p, g; NR planes), delta ring (interior), exchange planes
-    // (p_k, forward x and y weights, u'; 2 each), strip-end arrays (first
-    // p_k, last p_k, last forward x weight, first u'; 2 each), alignment slack
-    static constexpr size_t words =
-        (size_t)3 * NR * PLA + (size_t)NR * NIA + (size_t)4 * 2 * PL + (size_t)4 * 2 * PS + 32;
+    // words: ring (u: NRU planes, p and g: NR), delta ring (interior),
+    // exchange planes and strip-end arrays (2 buffers each).  Without RING:
+    // planes of p_k, forward x and y weights and u', arrays of the first p_k,
+    // last p_k, last forward x weight and first u' of each strip.  With RING,
+    // p_k and u' are written into the ring slots of p and u (neighbours read
+    // them there): planes of the forward x and y weights and the array of the
+    // last forward x weight remain.  Plus alignment slack.
+    static constexpr int NEP = RING ? 2 : 4, NES = RING ? 1 : 4;
+    static constexpr size_t words = (size_t)(NRU + 2 * NR) * PLA + (size_t)NR * NIA + (size_t)NEP * 2 * PL +
+                                    (size_t)NES * 2 * PS + 32;
     static constexpr size_t bytes = words * 4;
 };
 
-template <int TX, int TY, int V, int D>
+template <int TX, int TY, int V, int D, bool RING = false>
 constexpr size_t sweep5_smem_bytes() {
-    return Strip<TX, TY, V, D>::bytes;
+    return Strip<TX, TY, V, D, RING>::bytes;
 }
 
 // V-wide vector loads / stores (V = 4: 128-bit, V = 2: 64-bit).
@@ -218,10 +226,10 @@ struct StripState {
     float wzm[V];   // w(z-1, z)
 };
 
-template <int TX, int TY, int V, int NT, int D, int MINB, bool LOOP = false>
+template <int TX, int TY, int V, int NT, int D, int MINB, bool LOOP = false, bool RING = false>
 __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ SweepArgs A) {
-    using L = Strip<TX, TY, V, D>;
-    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR;
+    using L = Strip<TX, TY, V, D, RING>;
+    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR, NRU = L::NRU;
     constexpr int PLA = L::PLA, NIA = L::NIA;
     static_assert(V == 2 || V == 4, "strip width");
     static_assert(TX % V == 0, "tile width");
@@ -231,22 +239,23 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                       WS <= 256 && RY <= 256,
                   "TMA box");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[NR];
+    __shared__ __align__(8) uint64_t mbar[NRU];
     // ring planes start on 128-byte boundaries (TMA destinations)
     const uint32_t raw_base = (uint32_t)__cvta_generic_to_shared(smem_raw);
     unsigned char* smem = smem_raw + ((128u - (raw_base & 127u)) & 127u);
-    float* rU = reinterpret_cast<float*>(smem);                  // [NR][RY][WS] (stride PLA)
-    float* rP = rU + NR * PLA;                                   // [NR][RY][WS]
+    float* rU = reinterpret_cast<float*>(smem);                  // [NRU][RY][WS] (stride PLA)
+    float* rP = rU + NRU * PLA;                                  // [NR][RY][WS]
     uint32_t* rG = reinterpret_cast<uint32_t*>(rP + NR * PLA);  // [NR][RY][WS]
     float* rX = reinterpret_cast<float*>(rG + NR * PLA);        // [NR][TY][TX] (stride NIA)
-    float* ePK = rX + NR * NIA;                                  // [2][RY][WS]
-    float* eWY = ePK + 2 * PL;                                   // [2][RY][WS]
+    float* eWY = rX + NR * NIA;                                  // [2][RY][WS]
     float* eWX4 = eWY + 2 * PL;                                  // [2][RY][WS]
-    float* eUN = eWX4 + 2 * PL;                                  // [2][RY][WS]
-    float* ePF = eUN + 2 * PL;                                   // [2][RY][SX] first p_k of the strip
-    float* ePL = ePF + 2 * PS;                                   // [2][RY][SX] last p_k
-    float* eWX = ePL + 2 * PS;                                   // [2][RY][SX] last forward x weight
-    float* eUF = eWX + 2 * PS;                                   // [2][RY][SX] first u'
+    float* eWX = eWX4 + 2 * PL;                                  // [2][RY][SX] last forward x weight
+    // without RING only: p_k and u' planes, first / last p_k and first u' per strip
+    float* ePK = eWX + 2 * PS;                                   // [2][RY][WS]
+    float* eUN = ePK + 2 * PL;                                   // [2][RY][WS]
+    float* ePF = eUN + 2 * PL;                                   // [2][RY][SX]
+    float* ePL = ePF + 2 * PS;                                   // [2][RY][SX]
+    float* eUF = ePL + 2 * PS;                                   // [2][RY][SX]
     __shared__ double red[6 * (NT / 32)];
     __shared__ int s_last;
 
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
     const uint32_t sB = (uint32_t)__cvta_generic_to_shared(mbar);
     if (tid == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) mbar_init(sB + 8 * k, 1);
+        for (int k = 0; k < NRU; ++k) mbar_init(sB + 8 * k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -331,23 +340,25 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             float* Uo = u_out + base;
             float* Po = p_out + base;
 
-            // plane z of this work item is the CTA's load number q(z); it sits
-            // in ring slot q % NR and completes phase (q / NR) & 1 of its mbarrier
+            // plane z of this work item is the CTA's load number q(z); its p,
+            // g and delta sit in ring slot q % NR, its u in slot q % NRU, and it
+            // completes phase (q / NRU) & 1 of mbarrier q % NRU
             const uint32_t q0 = seq - (uint32_t)(z0 - 1);
             auto slot = [&](int z) { return (int)((q0 + (uint32_t)z) % NR); };
-            auto phase = [&](int z) { return ((q0 + (uint32_t)z) / NR) & 1u; };
+            auto slotu = [&](int z) { return (int)((q0 + (uint32_t)z) % NRU); };
+            auto phase = [&](int z) { return ((q0 + (uint32_t)z) / NRU) & 1u; };
             // TMA box origins: the tile's first strip and row (x = -V, y = -1)
             // for u, p, g; row y = 0 from column x = XC - V for delta
             const int cx = tx * TX, cy = ty * TY + 1;
             const int cz = box * A.pz + 2;
             auto issue = [&](int z) {
                 if (tid != 0) return;
-                const int sl = slot(z);
-                const uint32_t bar = sB + 8 * sl;
+                const int sl = slot(z), su = slotu(z);
+                const uint32_t bar = sB + 8 * su;
                 const bool wx = z >= z0 && z < z1;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_expect_tx(bar, (uint32_t)(3 * PL * 4 + (wx ? XW * TY * 4 : 0)));
-                tma_load3(sU + sl * PLA * 4, mu, cx, cy, cz + z, bar);
+                tma_load3(sU + su * PLA * 4, mu, cx, cy, cz + z, bar);
                 tma_load3(sP + sl * PLA * 4, mp, cx, cy, cz + z, bar);
                 tma_load3(sG + sl * PLA * 4, &A.tm.g, cx, cy, cz + z, bar);
                 if (wx) tma_load3(sX + sl * NIA * 4, &A.tm.x, cx + XC, cy + 1, cz + z, bar);
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             // plane z; `out` receives those for plane z+1.  BC = z & 1.
             auto step = [&](const int z, const StripState<V>& in, StripState<V>& out, auto bcc) {
                 constexpr int BC = decltype(bcc)::value, BN = BC ^ 1;
-                if (!waited_out && !mbar_wait(sB + 8 * slot(z + 1), phase(z + 1))) {
+                if (!waited_out && !mbar_wait(sB + 8 * slotu(z + 1), phase(z + 1))) {
                     waited_out = true;
                     if (A.err) atomicExch(A.err, 1);
                 }
@@ -372,7 +383,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 for (int i = 0; i < V; ++i) pkn[i] = wz0[i] = 0.0f, gn[i] = GC_ABSENT;
                 if (live) {
                     float uu[V], pp[V];
-                    ldv<V>(rU + sn * PLA + wofs, uu);
+                    ldv<V>(rU + slotu(z + 1) * PLA + wofs, uu);
                     ldv<V>(rP + sn * PLA + wofs, pp);
                     ldv<V>(rG + sn * PLA + wofs, gn);
 #pragma unroll
@@ -381,9 +392,13 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
 #pragma unroll
                         for (int i = 0; i < V; ++i) wz0[i] = wgt5(in.g0[i], gn[i], c2, wmin);
                     }
-                    stv<V>(ePK + BN * PL + wofs, pkn);
-                    ePF[BN * PS + sofs] = pkn[0];
-                    ePL[BN * PS + sofs] = pkn[V - 1];
+                    if constexpr (RING) {
+                        stv<V>(rP + sn * PLA + wofs, pkn);  // p_k replaces p in its slot
+                    } else {
+                        stv<V>(ePK + BN * PL + wofs, pkn);
+                        ePF[BN * PS + sofs] = pkn[0];
+                        ePL[BN * PS + sofs] = pkn[V - 1];
+                    }
                 }
 
                 // -- 2: stencil and update at plane z
@@ -392,12 +407,21 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 for (int i = 0; i < V; ++i) un0[i] = 0.0f;
                 if (sten && z >= z0) {
                     float uu[V], puu[V], pdd[V], wuu[V], wy0[V], wx0[V];
-                    ldv<V>(rU + slot(z) * PLA + wofs, uu);
-                    const float pl = ePL[BC * PS + sofs - 1];
-                    const float pr = has_right ? ePF[BC * PS + sofs + 1] : 0.0f;
+                    ldv<V>(rU + slotu(z) * PLA + wofs, uu);
+                    float pl, pr;
+                    if constexpr (RING) {
+                        const float* pk = rP + slot(z) * PLA;
+                        pl = pk[wofs - 1];
+                        pr = has_right ? pk[wofs + V] : 0.0f;
+                        ldv<V>(pk + wofs - WS, puu);
+                        ldv<V>(pk + wofs + WS, pdd);
+                    } else {
+                        pl = ePL[BC * PS + sofs - 1];
+                        pr = has_right ? ePF[BC * PS + sofs + 1] : 0.0f;
+                        ldv<V>(ePK + BC * PL + wofs - WS, puu);
+                        ldv<V>(ePK + BC * PL + wofs + WS, pdd);
+                    }
                     const float wl = eWX[BC * PS + sofs - 1];
-                    ldv<V>(ePK + BC * PL + wofs - WS, puu);
-                    ldv<V>(ePK + BC * PL + wofs + WS, pdd);
                     ldv<V>(eWY + BC * PL + wofs - WS, wuu);
                     ldv<V>(eWY + BC * PL + wofs, wy0);
                     ldv<V>(eWX4 + BC * PL + wofs, wx0);
@@ -416,8 +440,12 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                         const bool isfree = (int)in.g0[i] >= 0 && dv[i] > 0.0f;
                         un0[i] = isfree ? uu[i] - alpha * sv[i] * __fdividef(1.0f, dv[i]) : 0.0f;
                     }
-                    stv<V>(eUN + BC * PL + wofs, un0);
-                    eUF[BC * PS + sofs] = un0[0];
+                    if constexpr (RING) {
+                        stv<V>(rU + slotu(z) * PLA + wofs, un0);  // u' replaces u in its slot
+                    } else {
+                        stv<V>(eUN + BC * PL + wofs, un0);
+                        eUF[BC * PS + sofs] = un0[0];
+                    }
                     if (inner && z < z1) {
                         const int64_t pz = (int64_t)(z + 2) * plane;
                         float xn[V];
@@ -442,10 +470,17 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
 
                 // -- 3: delta over the edges owned by plane z-1 (+x, +y, +z)
                 if (inner && z - 1 >= z0) {
-                    const float ur = eUF[BN * PS + sofs + 1];
-                    float udd[V], unm[V], wxm[V], wym[V];
-                    ldv<V>(eUN + BN * PL + wofs + WS, udd);
-                    ldv<V>(eUN + BN * PL + wofs, unm);
+                    float ur, udd[V], unm[V], wxm[V], wym[V];
+                    if constexpr (RING) {
+                        const float* un = rU + slotu(z - 1) * PLA;
+                        ur = un[wofs + V];
+                        ldv<V>(un + wofs + WS, udd);
+                        ldv<V>(un + wofs, unm);
+                    } else {
+                        ur = eUF[BN * PS + sofs + 1];
+                        ldv<V>(eUN + BN * PL + wofs + WS, udd);
+                        ldv<V>(eUN + BN * PL + wofs, unm);
+                    }
                     ldv<V>(eWX4 + BN * PL + wofs, wxm);
                     ldv<V>(eWY + BN * PL + wofs, wym);
 #pragma unroll

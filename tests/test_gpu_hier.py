@@ -255,8 +255,10 @@ def test_leaf_in_host_memory_matches_hbm(rw):
     xyz, val = ph["labels_xyz"], ph["labels_value"]
     n0 = len(val) // 2
     out = []
-    for host, field in ((False, "pyramid"), (True, "pyramid"), (True, "hbm"), (False, "host")):
-        pyr = rw.rw_build_pyramid(ph["volume"], 16, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=host)
+    for host, field in ((False, "pyramid"), (True, "pyramid"), (True, "hbm"), (False, "host"), ("all", "pyramid"),
+                        (False, "host_all")):
+        pyr = rw.rw_build_pyramid(ph["volume"], 16, lo=0.0, hi=5000.0, normalize=True, leaf_in_host=host is True,
+                                  all_in_host=host == "all")
         leaf = pyr.read_level(pyr.levels - 1)
         tree = rw.Tree(pyr, rw.Opts(brick_size=16, beta=130.0, tol=1e-10, tile="32x8", leaf_field=field))
         tree.run(xyz[:n0], val[:n0])
@@ -651,3 +653,36 @@ def test_level_sharding_two_trees_match_oracle_and_unsharded(rw):
     det = determined_mask(levels[-1], 130.0)
     diff = np.abs(whole.read_level(pyr.levels - 1) - trees[0].read_level(pyr.levels - 1))
     assert np.max(diff[det]) <= TOL
+
+
+def test_all_levels_in_host_memory_match_oracle(rw):
+    """Out-of-core placement: every pyramid level and every tree field in
+    pinned, mapped host memory (the host input normalised in slabs).  A full
+    run and an incremental update match the oracle's H_p level by level, and
+    the device memory the pyramid and the tree take is below the size of
+    their own leaf field (they live in host memory; HBM holds the batched
+    solve's working set)."""
+    import torch
+    ph = P.vessel_tree(n=128, seed=9, n_segments=40)
+    xyz, val = ph["labels_xyz"], ph["labels_value"]
+    n0 = len(val) - 6
+    s = 16
+    torch.cuda.synchronize()
+    rw.release_workspace()
+    free0 = torch.cuda.mem_get_info()[0]
+    pyr = rw.rw_build_pyramid(ph["volume"], s, lo=0.0, hi=5000.0, normalize=True, all_in_host=True)
+    opts = rw.Opts(brick_size=s, beta=130.0, tol=HIER_TOL)
+    tree = rw.Tree(pyr, opts)
+    rw.release_workspace()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    assert used < 128 ** 3 * 4, used
+    tree.run(xyz[:n0], val[:n0])
+    tree.update_seeds(xyz[n0:], val[n0:])
+    q = O.quantize(ph["volume"], 0.0, 5000.0, True)
+    levels = O.pyramid(O.leaf_level(q), s)
+    for k in range(len(levels)):
+        assert np.array_equal(pyr.read_level(k), levels[k]), k
+    oo = hrw.Opts(brick_size=s, beta=130.0)
+    ot = hrw.run(levels, xyz[:n0], val[:n0], oo)
+    ou = hrw.update(ot, xyz[n0:], val[n0:])
+    _compare(rw, tree, ou, oo, s, incremental=True)
