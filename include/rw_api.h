@@ -159,7 +159,8 @@ enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, 
        RW_TILE_S64x14_D1 = 35,
        /* strips of 4 whose p_k and u' are exchanged through the load ring (_D: planes ahead) */
        RW_TILE_R64x14_D2 = 36, RW_TILE_R64x14_D1 = 37, RW_TILE_R64x11_D2 = 38, RW_TILE_R64x11_D3 = 39,
-       RW_TILE_R32x22_D2 = 40, RW_TILE_R32x20_D3 = 41 };
+       RW_TILE_R32x22_D2 = 40, RW_TILE_R32x20_D3 = 41, RW_TILE_R64x13_D3 = 42, RW_TILE_R64x12_D3 = 43,
+       RW_TILE_R40x20_D2 = 44, RW_TILE_R40x20_D3 = 45, RW_TILE_R40x8_D2 = 46 };
 
 typedef struct rw_stats {
     int32_t iters;          /* max PCG iterations over the systems of the call */

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -181,11 +182,12 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     } else if (nx <= 24) {
         c = {7};
     } else if (nx <= 48 || (nx % 40 == 0 && nx <= 160)) {
-        c = {TILE_S40x20, TILE_S40x8};
+        c = {TILE_S40x20, TILE_S40x8, TILE_R40x20_D2, TILE_R40x20_D3, TILE_R40x8_D2};
     } else {
         c = {TILE_S64x11,    TILE_S32x22,    TILE_S32x20,    TILE_S64x8,     TILE_S32x20_D3,
              TILE_S64x8_D3,  TILE_S32x22_D1, TILE_S64x8_D1,  TILE_S64x14_D1, TILE_R64x14_D2,
-             TILE_R64x14_D1, TILE_R64x11_D2, TILE_R64x11_D3, TILE_R32x22_D2, TILE_R32x20_D3};
+             TILE_R64x14_D1, TILE_R64x11_D2, TILE_R64x11_D3, TILE_R32x22_D2, TILE_R32x20_D3,
+             TILE_R64x13_D3, TILE_R64x12_D3};
     }
     std::vector<int> ok;
     for (int t : c)
@@ -326,6 +328,31 @@ void compact_cfg(const SweepCfg& full, int fp64, int gtype, int nz, int nact, in
 // grid-barrier state}.
 constexpr int kLoopIters = 512;
 
+// Host-side fault injection for tests of the failure path: RW_FAULT=grid_barrier
+// makes the looped sweep's grid barrier expect one arrival more than the grid
+// has, so every CTA's bounded wait runs out, the kernel flags it and returns,
+// and the call reports RW_ERR_TIMEOUT.  Read at every looped launch.
+bool fault_grid_barrier() {
+    const char* f = getenv("RW_FAULT");
+    return f && strcmp(f, "grid_barrier") == 0;
+}
+
+// Resident clusters of the cluster-resident solver for boxes of these dims
+// (0: not available), cached per dims.  RW_CLUSTER=0 in the environment turns
+// the cluster-resident mode off (the batched sweeps then finish every solve).
+int cluster_capacity(const Boxes& bx) {
+    const char* f = getenv("RW_CLUSTER");
+    if (f && strcmp(f, "0") == 0) return 0;
+    if (bx.nx > kClusterMaxDim || bx.ny > kClusterMaxDim || bx.nz > kClusterMaxDim || bx.nz < kClusterSize) return 0;
+    static std::map<std::array<int, 3>, int> cache;
+    const std::array<int, 3> key = {bx.nx, bx.ny, bx.nz};
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const int n = cluster_max_active(bx.nx, bx.ny, bx.nz, kClusterSize);
+    cache[key] = n;
+    return n;
+}
+
 rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, void* const u[2], void* const p[2],
                            int fp64, int gtype, int* n_active_dev, int n_act0, int* list_dev, size_t part_elems,
                            int64_t* sweeps, int64_t cap, double* ms_dev) {
@@ -337,6 +364,17 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     const int occ_loop = fp64 ? 0 : sweep5_occupancy_loop(cfg0.tile);
     bool loop = false;
     int lpar = 0;  // buffer parity of the next looped launch
+    // cluster-resident mode (FP32 sweeps in the strip kernels' padded layout,
+    // small boxes): once the active systems fit the resident clusters, the
+    // remaining iterations run there; each system keeps its buffer parity
+    const int cl_max = (!fp64 && cfg0.tile >= TILE_STRIP_FIRST && tile_margin(cfg0.tile) == 4)
+                           ? cluster_capacity(sa.bx) : 0;
+    bool clmode = false;
+    auto try_cluster = [&](int n) -> bool {
+        if (cl_max <= 0 || n > cl_max) return false;
+        clmode = true;
+        return true;
+    };
     auto use_cfg = [&](const SweepCfg& c) {
         cfg = c;
         sa.ntx = cfg.ntx;
@@ -390,6 +428,7 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
         n_cur = n_act;
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
+        if (clmode || try_cluster(n_act)) return RW_OK;
         if (try_loop(n_act)) return RW_OK;
         SweepCfg c2;
         compact_cfg(cfg0, fp64, gtype, sa.bx.nz, n_act, w->sms, part_elems, &c2);
@@ -397,7 +436,7 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
         return capture();
     };
     rw_status st = compact(n_act0);
-    if (st == RW_OK && !exec && !loop && !try_loop(n_cur)) st = capture();
+    if (st == RW_OK && !exec && !loop && !clmode && !try_cluster(n_act0) && !try_loop(n_cur)) st = capture();
     if (st != RW_OK) {
         if (exec) cudaGraphExecDestroy(exec);
         return st;
@@ -405,11 +444,40 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
-    int n_act = 1;
+    int n_act = std::max(1, n_act0);
     while (n_act > 0 && *sweeps < cap) {
         int64_t done = cfg.ipg;
         cudaError_t e = cudaSuccess;
-        if (loop) {
+        if (clmode) {
+            ClusterArgs ca;
+            ca.u[0] = static_cast<float*>(u[0]);
+            ca.u[1] = static_cast<float*>(u[1]);
+            ca.p[0] = static_cast<float*>(p[0]);
+            ca.p[1] = static_cast<float*>(p[1]);
+            ca.x = static_cast<float*>(sa.x);
+            ca.gc = sa.gc;
+            ca.px = sa.px;
+            ca.py = sa.py;
+            ca.pz = sa.pz;
+            ca.nx = sa.bx.nx;
+            ca.ny = sa.bx.ny;
+            ca.nz = sa.bx.nz;
+            ca.pls = (sa.bx.nx * sa.bx.ny + 3) & ~3;
+            ca.nzl = (sa.bx.nz + kClusterSize - 1) / kClusterSize;
+            ca.sc = sa.sc;
+            ca.list = sa.list;
+            ca.nlist = sa.nlist;
+            ca.nbox = sa.bx.nbox;
+            ca.n_active = n_active_dev;
+            ca.done = n_active_dev + 6;  // the "iterations done" word read back below
+            ca.loop_iters = (int)std::min<int64_t>(kLoopIters, cap - *sweeps);
+            ca.c2f = sa.c2f;
+            ca.wminf = sa.wminf;
+            const int ncl = std::max(1, std::min(cl_max, n_act > 0 ? n_act : n_cur));
+            e = cudaMemsetAsync(ca.done, 0, sizeof(int), w->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev0, w->stream);
+            if (e == cudaSuccess) e = launch_brick_cluster(ca, ncl, kClusterSize, w->stream);
+        } else if (loop) {
             sa.u_in = u[lpar];
             sa.p_in = p[lpar];
             sa.u_out = u[lpar ^ 1];
@@ -418,6 +486,7 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
             sa.loop_iters = (int)std::min<int64_t>(kLoopIters, cap - *sweeps);
             sa.loop_stop = list_dev && sa.bx.nbox >= 2 ? n_cur / 2 : 0;  // stop where compaction pays
             sa.gsync = reinterpret_cast<unsigned*>(n_active_dev + 2);
+            sa.barrier_extra = fault_grid_barrier() ? 1 : 0;
             st = strip_maps(cfg.tile, &sa, true);
             if (st != RW_OK) break;
             e = cudaMemsetAsync(sa.gsync, 0, 5 * sizeof(unsigned), w->stream);
@@ -439,7 +508,10 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
             break;
         }
         *ms_dev += ms;
-        if (loop) {
+        if (clmode) {
+            done = w->pinned[6];  // most iterations any system ran in the launch
+            g_launches += 1;
+        } else if (loop) {
             done = w->pinned[6];  // iterations the looped launch completed
             lpar = (int)((lpar + done) & 1);
             g_launches += 1;

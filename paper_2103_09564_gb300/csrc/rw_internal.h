@@ -73,6 +73,8 @@ struct SweepArgs {
     int loop_iters = 1;     // looped strip sweep: PCG iterations per launch
     int loop_stop = 0;      // looped strip sweep: stop once at most this many systems are active
     unsigned* gsync = nullptr;  // looped strip sweep: {arrivals, generation, go[2], iterations done}
+    int barrier_extra = 0;      // looped strip sweep: arrivals its grid barrier expects beyond the grid
+                                // (0; 1 only under the host's fault injection, so that every wait runs out)
     int sqrt_g = 0;         // Poisson weights: FP64 sweep reads sqrt(g) (the g words are packed so)
     StripMaps tm;           // k_sweep5 only
 };
@@ -86,8 +88,11 @@ enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE
               TILE_T32x12 = 28, TILE_T40x20 = 29, TILE_T40x8 = 30, TILE_S32x20_D3 = 31, TILE_S64x8_D3 = 32,
               TILE_S32x22_D1 = 33, TILE_S64x8_D1 = 34, TILE_S64x14_D1 = 35,
               // strips of 4 whose p_k and u' are exchanged through the TMA ring slots
-              TILE_R64x14_D2 = 36, TILE_R64x14_D1 = 37, TILE_R64x11_D2 = 38, TILE_R64x11_D3 = 39, TILE_R32x22_D2 = 40, TILE_R32x20_D3 = 41 };
-constexpr int N_TILES = 42;
+              TILE_R64x14_D2 = 36, TILE_R64x14_D1 = 37, TILE_R64x11_D2 = 38, TILE_R64x11_D3 = 39, TILE_R32x22_D2 = 40, TILE_R32x20_D3 = 41,
+              TILE_R64x13_D3 = 42, TILE_R64x12_D3 = 43,
+              // brick tiles (40-voxel boxes) with the ring exchange
+              TILE_R40x20_D2 = 44, TILE_R40x20_D3 = 45, TILE_R40x8_D2 = 46 };
+constexpr int N_TILES = 47;
 constexpr int TILE_RING_FIRST = TILE_R64x14_D2;  // k_sweep5 with the ring exchange
 constexpr int TILE_PADDED_FIRST = TILE_P32x12;  // tiles from here on use the padded layout (k_sweep4)
 constexpr int TILE_STRIP_FIRST = TILE_S64x11;   // tiles from here on: k_sweep5 (strips of 4, then of 2)
@@ -104,6 +109,34 @@ inline int tile_margin(int tile) {
 cudaError_t sweep5_launch_loop(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 int sweep5_occupancy_loop(int tile);
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s);
+
+// Cluster-resident PCG (cluster_kernel.cu): one thread-block cluster per
+// system, the system's FP32 state in the shared memory of its CTAs across the
+// iterations of a launch.  Systems of at most kClusterMaxDim voxels per axis
+// and at least as many z planes as CTAs per cluster, the strip kernels'
+// padded layout (x margin 4, y and z margins 2).
+constexpr int kClusterMaxDim = 40;
+constexpr int kClusterSize = 16;
+struct ClusterArgs {
+    float* u[2];              // u and p buffers by parity (BoxScalars::par)
+    float* p[2];
+    float* x;                 // FP32 correction delta
+    const uint32_t* gc;       // signed g words (+g free, -g seed, NaN absent)
+    int px, py, pz;           // padded box dims
+    int nx, ny, nz;           // box dims
+    int pls, nzl;             // shared-memory plane stride (floats) and planes per CTA
+    BoxScalars* sc;
+    const int* list;          // compacted active systems, or nullptr (all, skipping inactive)
+    const int* nlist;
+    int nbox;
+    int* n_active;            // decremented once per system that stops
+    int* done;                // max over systems of the iterations run in the launch
+    int loop_iters;           // iteration budget per system and launch
+    float c2f, wminf;         // weight parameters (as SweepArgs)
+};
+size_t cluster_smem_bytes(int nx, int ny, int nz, int cl);
+int cluster_max_active(int nx, int ny, int nz, int cl);
+cudaError_t launch_brick_cluster(const ClusterArgs& a, int nclusters, int cl, cudaStream_t s);
 size_t sweep_smem_bytes(int fp64, int tile);
 void tile_dims(int tile, int* tx, int* ty);
 int sweep_threads(int tile);

@@ -70,7 +70,8 @@ void tile_dims(int tile, int* tx, int* ty) {
                                       {64, 11}, {32, 22}, {32, 20}, {64, 8},  {40, 20}, {40, 8},
                                       {32, 20}, {64, 11}, {32, 12}, {40, 20}, {40, 8},  {32, 20},
                                       {64, 8},  {32, 22}, {64, 8},  {64, 14}, {64, 14}, {64, 14},
-                                      {64, 11}, {64, 11}, {32, 22}, {32, 20}};
+                                      {64, 11}, {64, 11}, {32, 22}, {32, 20}, {64, 13}, {64, 12},
+                                      {40, 20}, {40, 20}, {40, 8}};
     if (tile < 1 || tile >= N_TILES) tile = 1;
     *tx = T[tile][0];
     *ty = T[tile][1];
@@ -80,7 +81,7 @@ int sweep_threads(int tile) {
     static const int N[N_TILES] = {0,   512, 512, 320, 800, 640, 640, 256, 1024, 1024,
                                    512, 256, 256, 256, 288, 288, 576, 352, 352, 288,
                                    256, 256, 256, 224, 288, 160, 416, 480, 288, 512, 256, 256, 224, 256, 224,
-                                   320, 320, 320, 256, 256, 256, 256};
+                                   320, 320, 320, 256, 256, 256, 256, 288, 288, 288, 288, 160};
     return (tile >= 1 && tile < N_TILES) ? N[tile] : 0;
 }
 

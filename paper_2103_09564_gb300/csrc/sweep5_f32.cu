@@ -29,7 +29,12 @@ namespace {
     X(38, 64, 11, 4, 256, 2, 2, true)    \
     X(39, 64, 11, 4, 256, 3, 2, true)    \
     X(40, 32, 22, 4, 256, 2, 2, true)    \
-    X(41, 32, 20, 4, 256, 3, 2, true)
+    X(41, 32, 20, 4, 256, 3, 2, true)    \
+    X(42, 64, 13, 4, 288, 3, 2, true)    \
+    X(43, 64, 12, 4, 288, 3, 2, true)    \
+    X(44, 40, 20, 4, 288, 2, 2, true)    \
+    X(45, 40, 20, 4, 288, 3, 2, true)    \
+    X(46, 40, 8, 4, 160, 2, 3, true)
 
 template <int TX, int TY, int V, int NT, int D, int MB, bool R>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
@@ -51,25 +56,25 @@ int occupancy_one() {
     return n;
 }
 
-template <int TX, int TY, int V, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB, bool R = false>
 cudaError_t launch_loop_one(const SweepArgs& a, int grid, cudaStream_t s) {
-    auto fn = k_sweep5<TX, TY, V, NT, D, MB, true>;
+    auto fn = k_sweep5<TX, TY, V, NT, D, MB, true, R>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sweep5_smem_bytes<TX, TY, V, D>());
+                                         (int)sweep5_smem_bytes<TX, TY, V, D, R>());
     if (e != cudaSuccess) return e;
     SweepArgs arg = a;
     void* args[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(NT), args, sweep5_smem_bytes<TX, TY, V, D>(),
-                                       s);
+    return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(NT), args,
+                                       sweep5_smem_bytes<TX, TY, V, D, R>(), s);
 }
 
-template <int TX, int TY, int V, int NT, int D, int MB>
+template <int TX, int TY, int V, int NT, int D, int MB, bool R = false>
 int occupancy_loop_one() {
     int n = 0;
-    cudaFuncSetAttribute(k_sweep5<TX, TY, V, NT, D, MB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep5_smem_bytes<TX, TY, V, D>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, V, NT, D, MB, true>, NT,
-                                                  sweep5_smem_bytes<TX, TY, V, D>());
+    cudaFuncSetAttribute(k_sweep5<TX, TY, V, NT, D, MB, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep5_smem_bytes<TX, TY, V, D, R>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep5<TX, TY, V, NT, D, MB, true, R>, NT,
+                                                  sweep5_smem_bytes<TX, TY, V, D, R>());
     return n;
 }
 
@@ -82,6 +87,12 @@ cudaError_t sweep5_launch_loop(int tile, const SweepArgs& a, int grid, cudaStrea
         return launch_loop_one<40, 20, 4, 288, 2, 2>(a, grid, s);
     case 25:
         return launch_loop_one<40, 8, 4, 160, 2, 3>(a, grid, s);
+    case 44:
+        return launch_loop_one<40, 20, 4, 288, 2, 2, true>(a, grid, s);
+    case 45:
+        return launch_loop_one<40, 20, 4, 288, 3, 2, true>(a, grid, s);
+    case 46:
+        return launch_loop_one<40, 8, 4, 160, 2, 3, true>(a, grid, s);
     default:
         return cudaErrorInvalidValue;
     }
@@ -93,6 +104,12 @@ int sweep5_occupancy_loop(int tile) {
         return occupancy_loop_one<40, 20, 4, 288, 2, 2>();
     case 25:
         return occupancy_loop_one<40, 8, 4, 160, 2, 3>();
+    case 44:
+        return occupancy_loop_one<40, 20, 4, 288, 2, 2, true>();
+    case 45:
+        return occupancy_loop_one<40, 20, 4, 288, 3, 2, true>();
+    case 46:
+        return occupancy_loop_one<40, 8, 4, 160, 2, 3, true>();
     default:
         return 0;
     }

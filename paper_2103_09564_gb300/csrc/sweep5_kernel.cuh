@@ -60,10 +60,13 @@ struct Strip {
     static constexpr int WS = TX + 2 * V;       // words per row
     static constexpr int PL = RY * WS;          // words per plane
     static constexpr int PS = RY * SX;          // strips per plane
-    static constexpr int NR = D + 2;            // ring planes of p, g, delta
+    static constexpr int NR = D + 2;            // ring planes of p, delta (and g without RING)
     // ring planes of u: with RING, u' replaces u in its slot and is read one
     // step later (the delta of the plane behind), so the slot lives a step longer
     static constexpr int NRU = RING ? D + 3 : D + 2;
+    // ring planes of the g words: read only in the step before their plane is
+    // processed, so with RING their slot is free one step earlier
+    static constexpr int NRG = RING ? D + 1 : D + 2;
     static constexpr int NI = TX * TY;          // interior voxels
     // delta box: the interior (V = 4: its first column is 16-byte aligned),
     // or the full strip width from the halo strip (V = 2)
@@ -78,7 +81,7 @@ struct Strip {
     // them there): planes of the forward x and y weights and the array of the
     // last forward x weight remain.  Plus alignment slack.
     static constexpr int NEP = RING ? 2 : 4, NES = RING ? 1 : 4;
-    static constexpr size_t words = (size_t)(NRU + 2 * NR) * PLA + (size_t)NR * NIA + (size_t)NEP * 2 * PL +
+    static constexpr size_t words = (size_t)(NRU + NR + NRG) * PLA + (size_t)NR * NIA + (size_t)NEP * 2 * PL +
                                     (size_t)NES * 2 * PS + 32;
     static constexpr size_t bytes = words * 4;
 };
@@ -164,10 +167,13 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // calls it after the CTA's work): returns whether the next iteration runs,
 // i.e. whether more than `stop` systems are still active.
 // g = {arrivals, generation, go[2], iterations done}.  A wait that runs out
-// sets *err and returns false.
-__device__ __forceinline__ bool grid_step(unsigned* g, int it, const int* n_active, int stop, int* err) {
+// sets *err and returns false.  `extra`: arrivals expected beyond the grid
+// (0 in normal use; the fault injection of the host sets 1, so that no CTA is
+// the last arrival and every wait runs out).
+__device__ __forceinline__ bool grid_step(unsigned* g, int it, const int* n_active, int stop, int* err,
+                                          int extra) {
     __threadfence();
-    const unsigned target = gridDim.x * (unsigned)(it + 1);
+    const unsigned target = gridDim.x * (unsigned)(it + 1) + (unsigned)extra;
     const unsigned old = atomicAdd(&g[0], 1u);
     if (old == target - 1u) {
         __threadfence();  // the other CTAs' updates of n_active precede their arrivals
@@ -229,7 +235,8 @@ struct StripState {
 template <int TX, int TY, int V, int NT, int D, int MINB, bool LOOP = false, bool RING = false>
 __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ SweepArgs A) {
     using L = Strip<TX, TY, V, D, RING>;
-    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR, NRU = L::NRU;
+    constexpr int SX = L::SX, RY = L::RY, WS = L::WS, PL = L::PL, PS = L::PS, NR = L::NR, NRU = L::NRU,
+                  NRG = L::NRG;
     constexpr int PLA = L::PLA, NIA = L::NIA;
     static_assert(V == 2 || V == 4, "strip width");
     static_assert(TX % V == 0, "tile width");
@@ -245,8 +252,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
     unsigned char* smem = smem_raw + ((128u - (raw_base & 127u)) & 127u);
     float* rU = reinterpret_cast<float*>(smem);                  // [NRU][RY][WS] (stride PLA)
     float* rP = rU + NRU * PLA;                                  // [NR][RY][WS]
-    uint32_t* rG = reinterpret_cast<uint32_t*>(rP + NR * PLA);  // [NR][RY][WS]
-    float* rX = reinterpret_cast<float*>(rG + NR * PLA);        // [NR][TY][TX] (stride NIA)
+    uint32_t* rG = reinterpret_cast<uint32_t*>(rP + NR * PLA);  // [NRG][RY][WS]
+    float* rX = reinterpret_cast<float*>(rG + NRG * PLA);       // [NR][TY][TX] (stride NIA)
     float* eWY = rX + NR * NIA;                                  // [2][RY][WS]
     float* eWX4 = eWY + 2 * PL;                                  // [2][RY][WS]
     float* eWX = eWX4 + 2 * PL;                                  // [2][RY][SX] last forward x weight
@@ -346,6 +353,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             const uint32_t q0 = seq - (uint32_t)(z0 - 1);
             auto slot = [&](int z) { return (int)((q0 + (uint32_t)z) % NR); };
             auto slotu = [&](int z) { return (int)((q0 + (uint32_t)z) % NRU); };
+            auto slotg = [&](int z) { return (int)((q0 + (uint32_t)z) % NRG); };
             auto phase = [&](int z) { return ((q0 + (uint32_t)z) / NRU) & 1u; };
             // TMA box origins: the tile's first strip and row (x = -V, y = -1)
             // for u, p, g; row y = 0 from column x = XC - V for delta
@@ -360,7 +368,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 mbar_expect_tx(bar, (uint32_t)(3 * PL * 4 + (wx ? XW * TY * 4 : 0)));
                 tma_load3(sU + su * PLA * 4, mu, cx, cy, cz + z, bar);
                 tma_load3(sP + sl * PLA * 4, mp, cx, cy, cz + z, bar);
-                tma_load3(sG + sl * PLA * 4, &A.tm.g, cx, cy, cz + z, bar);
+                tma_load3(sG + slotg(z) * PLA * 4, &A.tm.g, cx, cy, cz + z, bar);
                 if (wx) tma_load3(sX + sl * NIA * 4, &A.tm.x, cx + XC, cy + 1, cz + z, bar);
             };
 
@@ -385,7 +393,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                     float uu[V], pp[V];
                     ldv<V>(rU + slotu(z + 1) * PLA + wofs, uu);
                     ldv<V>(rP + sn * PLA + wofs, pp);
-                    ldv<V>(rG + sn * PLA + wofs, gn);
+                    ldv<V>(rG + slotg(z + 1) * PLA + wofs, gn);
 #pragma unroll
                     for (int i = 0; i < V; ++i) pkn[i] = fmaf(bp, pp[i], ku * uu[i]);
                     if (sten) {
@@ -499,10 +507,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 // the halo, strip 0 needs its last x weight and row -1 its y
                 // weights; row TY+1 none.
                 if (live && ry < RY - 1) {
-                    const uint32_t gr = has_right ? rG[sn * PLA + wofs + V] : GC_ABSENT;
+                    const uint32_t* gpl = rG + slotg(z + 1) * PLA;
+                    const uint32_t gr = has_right ? gpl[wofs + V] : GC_ABSENT;
                     uint32_t gdd[V];
                     if (has_down) {
-                        ldv<V>(rG + sn * PLA + wofs + WS, gdd);
+                        ldv<V>(gpl + wofs + WS, gdd);
                     } else {
 #pragma unroll
                         for (int i = 0; i < V; ++i) gdd[i] = GC_ABSENT;
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         // TMA reads (async proxy) before the grid barrier releases them
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
         __syncthreads();
-        if (tid == 0) s_go = grid_step(A.gsync, it, A.n_active, A.loop_stop, A.err) ? 1 : 0;
+        if (tid == 0) s_go = grid_step(A.gsync, it, A.n_active, A.loop_stop, A.err, A.barrier_extra) ? 1 : 0;
         __syncthreads();
         if (!s_go) break;
     }

@@ -112,7 +112,7 @@ def test_ill_conditioned_chain_falls_back_to_fp64(rw):
                                   "s64x11", "s32x22", "s32x20", "s64x8", "s40x20", "s40x8", "t32x20", "t64x11",
                                   "t32x12", "t40x20", "t40x8", "s32x20_d3", "s64x8_d3", "s32x22_d1", "s64x8_d1",
                                   "s64x14_d1", "r64x14_d2", "r64x14_d1", "r64x11_d2", "r64x11_d3", "r32x22_d2",
-                                  "r32x20_d3"])
+                                  "r32x20_d3", "r64x13_d3", "r64x12_d3", "r40x20_d2", "r40x20_d3", "r40x8_d2"])
 def test_every_u16_tile_matches_oracle(rw, tile):
     c = P.plain_ball(n=48, seed=3)
     xo = _oracle(c, 130.0)
@@ -126,7 +126,7 @@ F32_TILES = ["32x16", "40x8", "40x20", "80x8", "80x16", "64x8", "32x8", "32x32",
              "p40x20", "p40x8", "p32x20", "s64x11", "s32x22", "s32x20", "s64x8", "s40x20",
              "s40x8", "t32x20", "t64x11", "t32x12", "t40x20", "t40x8", "s32x20_d3", "s64x8_d3",
              "s32x22_d1", "s64x8_d1", "s64x14_d1", "r64x14_d2", "r64x14_d1", "r64x11_d2", "r64x11_d3",
-             "r32x22_d2", "r32x20_d3"]
+             "r32x22_d2", "r32x20_d3", "r64x13_d3", "r64x12_d3", "r40x20_d2", "r40x20_d3", "r40x8_d2"]
 
 
 @pytest.mark.parametrize("tile", F32_TILES)
