@@ -72,8 +72,8 @@ __device__ __forceinline__ void cl_st4(uint32_t addr, float4 v) {
                  "f"(v.w)
                  : "memory");
 }
-__device__ __forceinline__ void cl_st_f64(uint32_t addr, double v) {
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+__device__ __forceinline__ void cl_st2(uint32_t addr, float a, float b) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
 }
 
 // Copy one plane (pls floats, a multiple of 4) to the same place in CTA `rank`.
@@ -83,18 +83,24 @@ __device__ __forceinline__ void plane_to(const float* src, const float* dst_loca
     for (int q = threadIdx.x; q < pls / 4; q += kClNT) cl_st4(dst + 16u * (uint32_t)q, s4[q]);
 }
 
+// The scalar state of a system during a launch (the FP64 fields of its
+// BoxScalars record as double-FP32 numbers).
+struct ClState {
+    DF gam, alpha, beta, rr, tol2;
+    int iters, max_iter, phase, active, status;
+};
+
 }  // namespace
 
 __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constant__ ClusterArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BoxScalars S;
-    __shared__ double red[6 * (kClNT / 32)];
-    __shared__ double vloc[6];
-    __shared__ int dummy_active;
+    __shared__ ClState T;
+    __shared__ DF wsum[6][kClNT / 32];
 
     const int tid = threadIdx.x;
     const int NX = A.nx, NY = A.ny, NZ = A.nz;
-    const int PLN = NX * NY, PLS = A.pls, NZL = A.nzl;
+    const int PLS = A.pls, NZL = A.nzl;
     const uint32_t rank = cl_rank(), CL = cl_size();
     const int z0 = (int)((rank * (uint32_t)NZ) / CL), z1 = (int)(((rank + 1) * (uint32_t)NZ) / CL);
     const int nzl = z1 - z0;
@@ -109,13 +115,19 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
     float* PKB = WZB + PLS;                          // p_k of plane z0-1
     float* PKA = PKB + PLS;                          // p_k of plane z1
     float* UA = PKA + PLS;                           // u' of plane z1
-    double* part = reinterpret_cast<double*>(UA + PLS);  // [CL][6] every CTA's sums
+    DF* part = reinterpret_cast<DF*>(UA + PLS);      // [CL][6] every CTA's sums
     const uint32_t part_s = (uint32_t)__cvta_generic_to_shared(part);
 
     const int64_t plane_g = (int64_t)A.px * A.py;
     const int64_t bstride = plane_g * A.pz;
     const int nlist = A.list ? *A.nlist : A.nbox;
-    const int nloc = nzl * PLN;
+    // voxel loops run over rows (plane, y) of the own planes: thread tid owns
+    // column x = tid % NX of rows tid / NX, tid / NX + RPI, ... (no division
+    // per voxel; threads beyond RPI * NX idle in the loops)
+    const int RPI = kClNT / NX;
+    const int tx = tid % NX, trow = tid / NX;
+    const bool tlive = trow < RPI;
+    const int nrows = nzl * NY;
 
     for (int li = (int)cl_id(); li < nlist; li += (int)cl_count()) {
         const int box = A.list ? A.list[li] : li;
@@ -124,6 +136,18 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
         if (tid == 0) scalars_load_cg(Sg, &S);
         __syncthreads();
         if (!S.active) continue;  // the same record in every CTA: a uniform skip
+        if (tid == 0) {
+            T.gam = df_of(S.gam);
+            T.alpha = df_of(S.alpha);
+            T.beta = df_of(S.beta);
+            T.rr = df_of(S.rr);
+            T.tol2 = df_of(S.tol2);
+            T.iters = S.iters;
+            T.max_iter = S.max_iter;
+            T.phase = S.phase;
+            T.active = S.active;
+            T.status = S.status;
+        }
         const int par = S.par;
         float* ug = A.u[par];
         float* pg = A.p[par];
@@ -132,8 +156,10 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
         const int64_t gbase = (int64_t)box * bstride;
 
         // state of the own planes; weights and diagonal from the g words
-        for (int i = tid; i < nloc; i += kClNT) {
-            const int lz = i / PLN, r = i - lz * PLN, y = r / NX, x = r - y * NX;
+        for (int row = tlive ? trow : nrows, lz = row / NY, y = row - lz * NY; row < nrows;
+             row += RPI, y += RPI) {
+            while (y >= NY) y -= NY, ++lz;
+            const int x = tx, r = y * NX + x;
             const int o = lz * PLS + r;
             // padded layout: x margin 4, y and z margins 2, margins absent
             const int64_t gi = gbase + (int64_t)(z0 + lz + 2) * plane_g + (int64_t)(y + 2) * A.px + (x + 4);
@@ -159,14 +185,12 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
 
         int it = 0;
         for (;;) {
-            const float alpha = (float)S.alpha;
-            const bool keep = S.phase == 2;
-            const float ku = keep ? 0.0f : 1.0f, bp = keep ? 1.0f : (float)S.beta;
+            const float alpha = T.alpha.hi + T.alpha.lo;
+            const bool keep = T.phase == 2;
+            const float ku = keep ? 0.0f : 1.0f, bp = keep ? 1.0f : T.beta.hi + T.beta.lo;
             // -- A: p_k = ku u + bp p, boundary planes to the neighbours
-            for (int i = tid; i < nloc; i += kClNT) {
-                const int lz = i / PLN, r = i - lz * PLN, o = lz * PLS + r;
-                Pk[o] = fmaf(bp, Pk[o], ku * U[o]);
-            }
+            // (the few padding words of each plane are updated too, and never read)
+            for (int i = tid; i < nzl * PLS; i += kClNT) Pk[i] = fmaf(bp, Pk[i], ku * U[i]);
             __syncthreads();
             if (nzl > 0) {
                 if (rank > 0) plane_to(Pk, PKA, rank - 1, PLS);
@@ -175,8 +199,10 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
             cl_sync();
             // -- B: stencil, update, five of the six inner products
             float a_gam = 0.f, a_rr = 0.f, a_del = 0.f, a_eps = 0.f, a_pi = 0.f, a_tau = 0.f;
-            for (int i = tid; i < nloc; i += kClNT) {
-                const int lz = i / PLN, r = i - lz * PLN, y = r / NX, x = r - y * NX;
+            for (int row = tlive ? trow : nrows, lz = row / NY, y = row - lz * NY; row < nrows;
+                 row += RPI, y += RPI) {
+                while (y >= NY) y -= NY, ++lz;
+                const int x = tx, r = y * NX + x;
                 const int o = lz * PLS + r;
                 const float p0 = Pk[o];
                 const float pL = x > 0 ? Pk[o - 1] : 0.0f, wL = x > 0 ? WX[o - 1] : 0.0f;
@@ -203,8 +229,10 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
             if (nzl > 0 && rank > 0) plane_to(U, UA, rank - 1, PLS);
             cl_sync();
             // -- C: delta = u'^T A u' over the forward edges of the own voxels
-            for (int i = tid; i < nloc; i += kClNT) {
-                const int lz = i / PLN, r = i - lz * PLN, y = r / NX, x = r - y * NX;
+            for (int row = tlive ? trow : nrows, lz = row / NY, y = row - lz * NY; row < nrows;
+                 row += RPI, y += RPI) {
+                while (y >= NY) y -= NY, ++lz;
+                const int x = tx, r = y * NX + x;
                 const int o = lz * PLS + r;
                 const float un = U[o];
                 if (x + 1 < NX) {
@@ -218,34 +246,96 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
                 const float dz = un - (lz + 1 < nzl ? U[o + PLS] : UA[r]);
                 a_del = fmaf(WZ[o] * dz, dz, a_del);
             }
-            const float fv[6] = {a_gam, a_rr, a_del, a_eps, a_pi, a_tau};
-            double v[6];
-            block_reduce_f32<kClNT, 6>(fv, v, red);
-            if (tid == 0)
+            // six sums: warp trees, then a tree over the warps, in double-FP32
+            {
+                DF v[6] = {{a_gam, 0.f}, {a_rr, 0.f}, {a_del, 0.f}, {a_eps, 0.f}, {a_pi, 0.f}, {a_tau, 0.f}};
 #pragma unroll
-                for (int k = 0; k < 6; ++k) vloc[k] = v[k];
-            __syncthreads();
-            // this CTA's sums into slot `rank` of every CTA's table
-            if (tid < 6 * (int)CL) {
-                const uint32_t to = (uint32_t)tid / 6u, k = (uint32_t)tid % 6u;
-                cl_st_f64(cl_map(part_s + 8u * (rank * 6u + k), to), vloc[k]);
+                for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+                const int lane = tid & 31, wid = tid >> 5;
+                if (lane == 0)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) wsum[k][wid] = v[k];
+                __syncthreads();
+                if (wid == 0) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) v[k] = lane < kClNT / 32 ? wsum[k][lane] : DF{0.f, 0.f};
+#pragma unroll
+                    for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+                    // this CTA's sums into slot `rank` of every CTA's table (lane t: CTA t)
+                    if (lane < (int)CL) {
+                        const uint32_t dst = cl_map(part_s, (uint32_t)lane) + 8u * 6u * rank;
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) cl_st2(dst + 8u * k, v[k].hi, v[k].lo);
+                    }
+                }
             }
             cl_sync();
-            if (tid == 0) {
-                double tv[6] = {0, 0, 0, 0, 0, 0};
-                for (uint32_t q = 0; q < CL; ++q)
+            // every CTA: the cluster's sums (a tree over the CTAs, the same order
+            // everywhere) and the scalar recurrences, in warp 0
+            if (tid < 32) {
+                DF v[6];
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) tv[k] += part[q * 6 + k];
-                finalize_box(&S, tv, &dummy_active, par);  // par unchanged: the state returns to its buffer
+                for (int k = 0; k < 6; ++k) v[k] = tid < (int)CL ? part[tid * 6 + k] : DF{0.f, 0.f};
+#pragma unroll
+                for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+                if (tid == 0) {
+                    // the recurrences of the strip kernels' last CTA (finalize_box)
+                    const DF g = v[0], rr = v[1], dl = v[2], ep = v[3], pi = v[4], tau = v[5];
+                    bool stop;
+                    T.rr = rr;
+                    if (T.phase == 0) {
+                        T.phase = 1;
+                        T.gam = g;
+                        stop = !df_gt(rr, T.tol2) || !df_pos(g) || !df_pos(dl);
+                        T.alpha = stop ? DF{0.f, 0.f} : df_div(g, dl);
+                        T.beta = DF{0.f, 0.f};
+                    } else {
+                        if (T.phase == 1) T.iters += 1;
+                        T.phase = 1;
+                        const DF bcg = df_pos(pi) ? df_neg(df_div(ep, pi)) : DF{0.f, 0.f};
+                        const DF den = df_add(df_add(dl, df_mul(DF{2.f, 0.f}, df_mul(bcg, ep))),
+                                              df_mul(df_mul(bcg, bcg), pi));
+                        const DF num = df_add(g, df_mul(bcg, tau));
+                        const bool ok = df_pos(pi) && df_pos(den) && df_pos(num);
+                        const bool above = df_gt(rr, T.tol2);
+                        stop = !above || T.iters >= T.max_iter || !ok;
+                        if (!ok && above) T.status = 5;
+                        if (!stop) {
+                            T.beta = bcg;
+                            T.alpha = df_div(num, den);
+                            T.gam = g;
+                        }
+                    }
+                    if (stop) T.active = 0;
+                }
             }
             __syncthreads();
             ++it;
-            if (!S.active || it >= A.loop_iters) break;  // identical in every CTA
+            if (!T.active || it >= A.loop_iters) break;  // identical in every CTA
         }
+        if (tid == 0) {  // the record as FP64, buffer parity unchanged
+            S.gam = df_dbl(T.gam);
+            S.alpha = df_dbl(T.alpha);
+            S.beta = df_dbl(T.beta);
+            S.rr = df_dbl(T.rr);
+            S.iters = T.iters;
+            S.phase = T.phase;
+            S.active = T.active;
+            S.status = T.status;
+        }
+        __syncthreads();
 
         // write the state back into the system's buffer
-        for (int i = tid; i < nloc; i += kClNT) {
-            const int lz = i / PLN, r = i - lz * PLN, y = r / NX, x = r - y * NX;
+        for (int row = tlive ? trow : nrows, lz = row / NY, y = row - lz * NY; row < nrows;
+             row += RPI, y += RPI) {
+            while (y >= NY) y -= NY, ++lz;
+            const int x = tx, r = y * NX + x;
             const int o = lz * PLS + r;
             const int64_t gi = gbase + (int64_t)(z0 + lz + 2) * plane_g + (int64_t)(y + 2) * A.px + (x + 4);
             ug[gi] = U[o];
@@ -264,7 +354,7 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
 size_t cluster_smem_bytes(int nx, int ny, int nz, int cl) {
     const int pls = ((nx * ny) + 3) & ~3;
     const int nzl = (nz + cl - 1) / cl;
-    return ((size_t)7 * nzl * pls + (size_t)4 * pls) * sizeof(float) + (size_t)cl * 6 * sizeof(double);
+    return ((size_t)7 * nzl * pls + (size_t)4 * pls) * sizeof(float) + (size_t)cl * 6 * 2 * sizeof(float);
 }
 
 // Clusters of `cl` CTAs that can be resident at once (0: the launch is not possible).

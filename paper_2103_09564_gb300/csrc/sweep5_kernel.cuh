@@ -552,13 +552,17 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             if (z <= z1) step(z, sa, sb, std::integral_constant<int, 0>());
             seq += (uint32_t)(z1 - z0 + 3);  // planes z0-1 .. z1+1
         }
+        // the six sums in double-FP32 (FP32 pipes: on GB300 a chain of
+        // dependent FP64 operations here would sit on every sweep's critical
+        // path); per-CTA partials are (hi, lo) float pairs in the 8-byte slots
         const float fv[6] = {a_gam, a_rr, a_del, a_eps, a_pi, a_tau};
-        double v[6];
-        block_reduce_f32<NT, 6>(fv, v, red);
+        DF v[6];
+        DF* redf = reinterpret_cast<DF*>(red);
+        block_reduce_df<NT, 6>(fv, v, redf);
         if (tid == 0) {
-            double* pp = A.partials + ((int64_t)li * tpb + t) * 6;
+            float2* pp = reinterpret_cast<float2*>(A.partials + ((int64_t)li * tpb + t) * 6);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) pp[k] = v[k];
+            for (int k = 0; k < 6; ++k) pp[k] = make_float2(v[k].hi, v[k].lo);
             __threadfence();
             const unsigned prev = atomicAdd(&S->counter, 1u);
             s_last = (prev == (unsigned)tpb - 1u);
@@ -566,23 +570,28 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         __syncthreads();
         if (s_last) {
             __threadfence();
-            double tv[6] = {0, 0, 0, 0, 0, 0};
-            const double* pb = A.partials + (int64_t)li * tpb * 6;
+            DF tv[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) tv[j] = DF{0.0f, 0.0f};
+            const float2* pb = reinterpret_cast<const float2*>(A.partials + (int64_t)li * tpb * 6);
             for (int k = tid; k < tpb; k += NT)
 #pragma unroll
-                for (int j = 0; j < 6; ++j) tv[j] += __ldcg(pb + 6 * k + j);
-            block_reduce<NT, 6>(tv, red);
+                for (int j = 0; j < 6; ++j) {
+                    const float2 q = __ldcg(pb + 6 * k + j);
+                    tv[j] = df_add(tv[j], DF{q.x, q.y});
+                }
+            block_reduce_df2<NT, 6>(tv, redf);
             if (tid == 0) {
                 if constexpr (LOOP) {
                     // the record as other CTAs left it, updated in registers
                     BoxScalars loc;
                     scalars_load_cg(S, &loc);
                     loc.counter = 0u;
-                    finalize_box(&loc, tv, A.n_active, out_par);
+                    finalize_box_df(&loc, tv, A.n_active, out_par);
                     scalars_store(S, loc);
                 } else {
                     S->counter = 0u;
-                    finalize_box(S, tv, A.n_active, out_par);
+                    finalize_box_df(S, tv, A.n_active, out_par);
                 }
             }
         }

@@ -125,6 +125,137 @@ __device__ __forceinline__ void block_reduce_f32(const float* f, double* v, doub
     __syncthreads();
 }
 
+// Double-FP32 numbers (hi + lo, about 48 significant bits) for the per-iteration
+// sums and scalar recurrences: on GB300 a dependent chain of FP64 operations
+// costs far more than the sweep of a small system, FP32 operations do not.
+// Addition is Knuth's TwoSum, products use the exact FMA remainder (Dekker's
+// product with a fused multiply-add), division one correction step.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_fast(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return df_fast(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = a.hi / b.hi;
+    const DF r = df_add(a, df_mul(DF{-q1, 0.0f}, b));
+    return df_fast(q1, r.hi / b.hi);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ bool df_pos(DF a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
+__device__ __forceinline__ bool df_gt(DF a, DF b) { return df_pos(df_add(a, df_neg(b))); }
+__device__ __forceinline__ DF df_of(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_dbl(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_shfl_xor(DF a, int m) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
+// Block-wide double-FP32 sums of NV per-thread FP32 values: each warp's 32
+// lanes in a shuffle tree, then the warp sums in a tree of warp 0.  The
+// result is valid in thread 0.  red: NV * (NT / 32) DF values.
+template <int NT, int NV>
+__device__ __forceinline__ void block_reduce_df(const float* f, DF* v, DF* red) {
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = DF{f[k], 0.0f};
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k * NW + wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = lane < NW ? red[k * NW + lane] : DF{0.0f, 0.0f};
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+    }
+    __syncthreads();
+}
+
+// Same for per-thread double-FP32 values.
+template <int NT, int NV>
+__device__ __forceinline__ void block_reduce_df2(DF* v, DF* red) {
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k * NW + wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = lane < NW ? red[k * NW + lane] : DF{0.0f, 0.0f};
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
+    }
+    __syncthreads();
+}
+
+// finalize_box (below) in double-FP32: the same recurrences and decisions on
+// the six sums of a sweep, without a chain of dependent FP64 operations (the
+// record keeps FP64 fields; they are converted on the way in and out).
+template <typename SP>
+__device__ __forceinline__ void finalize_box_df(SP S, const DF* v, int* n_active, int out_par) {
+    const DF g = v[0], rr = v[1], dl = v[2], ep = v[3], pi = v[4], tau = v[5];
+    const DF tol2 = df_of(S->tol2);
+    bool stop;
+    S->par = out_par;
+    S->rr = df_dbl(rr);
+    if (S->phase == 0) {
+        // restart sweep (alpha = beta = 0, p = u): alpha_0 = gamma_0 / delta_0
+        S->phase = 1;
+        S->gam = df_dbl(g);
+        stop = !df_gt(rr, tol2) || !df_pos(g) || !df_pos(dl);
+        S->alpha = stop ? 0.0 : df_dbl(df_div(g, dl));
+        S->beta = 0.0;
+    } else {
+        if (S->phase == 1) S->iters += 1;
+        S->phase = 1;
+        const DF bcg = df_pos(pi) ? df_neg(df_div(ep, pi)) : DF{0.0f, 0.0f};
+        const DF den = df_add(df_add(dl, df_mul(DF{2.0f, 0.0f}, df_mul(bcg, ep))), df_mul(df_mul(bcg, bcg), pi));
+        const DF num = df_add(g, df_mul(bcg, tau));
+        const bool ok = df_pos(pi) && df_pos(den) && df_pos(num);
+        const bool above = df_gt(rr, tol2);
+        stop = !above || S->iters >= S->max_iter || !ok;
+        if (!ok && above) S->status = 5;
+        if (!stop) {
+            S->beta = df_dbl(bcg);
+            S->alpha = df_dbl(df_div(num, den));
+            S->gam = df_dbl(g);
+        }
+    }
+    if (stop) {
+        S->active = 0;
+        atomicSub(n_active, 1);
+    }
+}
+
 // Scalar recurrences of the system after its sweep (run by one thread of the
 // last CTA).  v = {gamma, ||r||^2, delta, eps, pi, tau} of the sweep that
 // produced u = u_k+1 from the direction p = p_k:
