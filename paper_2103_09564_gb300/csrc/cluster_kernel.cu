@@ -5,7 +5,7 @@
 // The batched sweeps stream every system through HBM / L2 once per iteration;
 // when only a few systems are left (the slow bricks of a level, the small
 // coarse levels), an iteration costs the latency of its loads, of the
-// two-stage FP64 reduction and of a grid-wide synchronisation, about ten
+// two-stage reduction and of a grid-wide synchronisation, about ten
 // microseconds, whatever the size.  Here the z planes of a system are split
 // over the CL CTAs of a cluster (CL = 16, non-portable cluster size, one CTA
 // per SM): every CTA holds u, p_k, the correction delta, the diagonal and the
@@ -19,7 +19,8 @@
 //
 // One iteration is the sweep of the strip kernels (same recurrences,
 // single-reduction PCG with u = D^-1 r stored, difference-form stencil, FP32
-// per-thread partial sums, FP64 block and cluster sums): p_k = ku u + bp p,
+// per-thread partial sums, double-FP32 block and cluster sums and scalar
+// recurrences): p_k = ku u + bp p,
 // s = A p_k, u' = u - alpha D^-1 s (free voxels), delta += alpha p_k, and
 // gamma, ||D u'||^2, u'^T A u', (u', s), (p_k, s), (D u', p_k).  A launch runs
 // up to `loop_iters` iterations of each system; the state is read from and

@@ -356,6 +356,10 @@ __global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, d
     const double tgt = tol * tol * S->bb;
     const bool need = S->nseed > 0 && S->nfree > 0 && S->bb > 0.0 && S->rr_true > tgt && S->iters < max_iter;
     S->counter = 0u;
+    // the residual that precedes every round wrote u (and the kept p) into
+    // buffer 0: the record must point there, for the sweeps that read the
+    // system's own parity (the cluster-resident solver)
+    S->par = 0;
     if (need) {
         S->active = 1;
         // continue the Krylov process across the residual replacement when

@@ -169,6 +169,46 @@ def test_batch_of_volumes(rw):
         assert np.max(np.abs(x[b] - _oracle(c, 130.0))) <= TOL
 
 
+@pytest.mark.parametrize("variant", range(4))
+def test_cluster_resident_rounds_continue_from_the_fp64_residual(rw, monkeypatch, variant):
+    # 12 systems of 32^3, more than the resident 16-CTA clusters: each round
+    # starts in the batched strip sweeps (which alternate the buffer parity
+    # every sweep) and finishes in the cluster-resident solver (which goes on
+    # from the system's own parity).  Six systems start near their solution
+    # and finish in the first refinement round, so the second round of the six
+    # cold ones runs in the cluster-resident solver from its first sweep.  The
+    # FP64 residual between rounds moves every system to buffer 0; a round
+    # that read the buffer of the last sweep instead would iterate on an old
+    # residual, end short of the tolerance and fall back to FP64 sweeps.  The
+    # warm starts' distance varies the parity at which the six cold systems
+    # enter the cluster-resident solver.  Both modes must converge in FP32
+    # rounds alone, in about the same number of iterations, to the oracle.
+    n = 12
+    cs = [P.ball_case(n=32, seed=60 + n * variant + s, radius=8.0 + (s % 4), ellipsoid=(s % 2 == 1))
+          for s in range(n)]
+    vol, code, val = (_cuda(np.stack([c[k] for c in cs])) for k in ("volume", "code", "value"))
+    monkeypatch.setenv("RW_CLUSTER", "0")
+    xr, _ = rw.rw_solve(vol, code, val, rw.Opts(beta=130.0, tol=1e-10, tile="s40x20"))
+    x0 = xr.cpu().numpy()
+    warm = np.arange(n) % 2 == 0
+    rs = np.random.default_rng(variant)
+    x0[warm] += np.float32(10.0 ** (-7 + 0.5 * variant)) * rs.standard_normal(x0[warm].shape).astype(np.float32)
+    x0[~warm] = 0.0
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("RW_CLUSTER", mode)
+        x, st = rw.rw_solve(vol, code, val, rw.Opts(beta=130.0, tol=1e-10, tile="s40x20"), x0=_cuda(x0))
+        assert st["fp64_fallbacks"] == 0, (mode, st)
+        assert st["refine_rounds"] >= 2 and st["rel_resid"] <= 1e-10
+        out[mode] = (x.cpu().numpy().astype(np.float64), st)
+    (xs, ss), (xc, sc) = out["0"], out["1"]
+    assert not np.array_equal(xs, xc)           # the cluster-resident solver ran
+    assert abs(sc["iters"] - ss["iters"]) <= 0.15 * ss["iters"]
+    assert np.max(np.abs(xs - xc)) <= 1e-6
+    for b in (1, 6):
+        assert np.max(np.abs(xc[b] - _oracle(cs[b], 130.0))) <= TOL
+
+
 def test_host_pointers_equal_device_pointers(rw):
     # one fixed tile: an autotuning call runs its tuning sweeps as real
     # iterations and rounds differently from a call with a cached choice
