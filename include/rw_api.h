@@ -142,19 +142,16 @@ typedef struct rw_opts {
  *     and rw_solve_noalloc return RW_ERR_UNIMPLEMENTED. */
 typedef enum { RW_WEIGHT_GAUSSIAN = 0, RW_WEIGHT_POISSON = 1 } rw_weight;
 
-enum { RW_TILE_AUTO = 0, RW_TILE_32x16 = 1, RW_TILE_64x8 = 2, RW_TILE_40x8 = 3, RW_TILE_40x20 = 4,
-       RW_TILE_80x8 = 5, RW_TILE_80x16 = 6, RW_TILE_32x8 = 7, RW_TILE_32x32 = 8, RW_TILE_64x16 = 9,
-       /* warp-row tiles (28 columns + halo = one warp per row; FP32 only) */
-       RW_TILE_W28x28 = 10, RW_TILE_W28x12 = 11, RW_TILE_W28x20 = 12, RW_TILE_W28x28_8W = 13,
-       /* padded-layout tiles (16-byte asynchronous row copies; FP32 only, the default family) */
-       RW_TILE_P32x12 = 14, RW_TILE_P32x12_DEEP = 15, RW_TILE_P32x28 = 16, RW_TILE_P40x20 = 17,
-       RW_TILE_P40x8 = 18, RW_TILE_P32x20 = 19,
-       /* register-blocked strips of 4 voxels (padded layout, x margin 4) */
+/* Sweep tiles (rw_opts.tile).  Any other value, or a tile of the other
+ * precision, is rejected with RW_ERR_INVALID_ARG. */
+enum { RW_TILE_AUTO = 0,
+       /* FP64 sweeps (RW_FP64 and the FP64 fallback); 32x8 is also the FP32
+        * tile for boxes narrower than 25 voxels in x */
+       RW_TILE_40x8 = 3, RW_TILE_32x8 = 7,
+       /* FP32 register-blocked strips of 4 voxels (padded layout, x margin 4):
+        * 2 planes in flight, 3 (_D3) or 1 (_D1; s64x14_d1: 320 threads) */
        RW_TILE_S64x11 = 20, RW_TILE_S32x22 = 21, RW_TILE_S32x20 = 22, RW_TILE_S64x8 = 23,
        RW_TILE_S40x20 = 24, RW_TILE_S40x8 = 25,
-       /* register-blocked strips of 2 voxels (padded layout, x margin 2) */
-       RW_TILE_T32x20 = 26, RW_TILE_T64x11 = 27, RW_TILE_T32x12 = 28, RW_TILE_T40x20 = 29, RW_TILE_T40x8 = 30,
-       /* strips of 4 with 3 planes in flight (_D3) or 1 (_D1; s64x14_d1: 320 threads) */
        RW_TILE_S32x20_D3 = 31, RW_TILE_S64x8_D3 = 32, RW_TILE_S32x22_D1 = 33, RW_TILE_S64x8_D1 = 34,
        RW_TILE_S64x14_D1 = 35,
        /* strips of 4 whose p_k and u' are exchanged through the load ring (_D: planes ahead) */

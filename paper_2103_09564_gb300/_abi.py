@@ -21,14 +21,10 @@ RW_NODE_SOLVED, RW_NODE_PRUNABLE, RW_NODE_HOM, RW_NODE_DT, RW_NODE_CFL, RW_NODE_
     RW_NODE_CFL_ADDED, RW_NODE_NO_SEEDS, RW_NODE_CHANGED = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
 RW_NOALLOC_MAX_VOXELS = 262144
 RW_NOALLOC_MAX_BATCH = 64
-RW_TILE = {"auto": 0, "32x16": 1, "64x8": 2, "40x8": 3, "40x20": 4, "80x8": 5, "80x16": 6, "32x8": 7, "32x32": 8,
-           "64x16": 9, "w28x28": 10, "w28x12": 11, "w28x20": 12, "w28x28_8w": 13, "p32x12": 14, "p32x12_deep": 15,
-           "p32x28": 16, "p40x20": 17, "p40x8": 18, "p32x20": 19, "s64x11": 20, "s32x22": 21, "s32x20": 22,
-           "s64x8": 23, "s40x20": 24, "s40x8": 25, "t32x20": 26, "t64x11": 27, "t32x12": 28, "t40x20": 29,
-           "t40x8": 30, "s32x20_d3": 31, "s64x8_d3": 32, "s32x22_d1": 33, "s64x8_d1": 34, "s64x14_d1": 35,
+RW_TILE = {"auto": 0, "40x8": 3, "32x8": 7, "s64x11": 20, "s32x22": 21, "s32x20": 22, "s64x8": 23, "s40x20": 24,
+           "s40x8": 25, "s32x20_d3": 31, "s64x8_d3": 32, "s32x22_d1": 33, "s64x8_d1": 34, "s64x14_d1": 35,
            "r64x14_d2": 36, "r64x14_d1": 37, "r64x11_d2": 38, "r64x11_d3": 39, "r32x22_d2": 40, "r32x20_d3": 41,
-           "r64x13_d3": 42, "r64x12_d3": 43,
-           "r40x20_d2": 44, "r40x20_d3": 45, "r40x8_d2": 46}
+           "r64x13_d3": 42, "r64x12_d3": 43, "r40x20_d2": 44, "r40x20_d3": 45, "r40x8_d2": 46}
 
 # every function declared in include/rw_api.h
 EXPORTS = ["rw_opts_default", "rw_last_error", "rw_version", "rw_release_workspace", "rw_solve", "rw_solve_noalloc",

@@ -142,6 +142,8 @@ rw_status check_opts(const rw_opts& o) {
         (o.weight != RW_WEIGHT_GAUSSIAN && o.weight != RW_WEIGHT_POISSON) || o.leaf_field < RW_LEAF_AS_PYRAMID ||
         o.leaf_field > RW_FIELDS_HOST)
         return fail(RW_ERR_INVALID_ARG, "invalid rw_opts");
+    if (o.tile != RW_TILE_AUTO && !tile_compiled(o.precision == RW_FP64, o.tile))
+        return fail(RW_ERR_INVALID_ARG, "tile %d is not a sweep tile of this precision", o.tile);
     return RW_OK;
 }
 
@@ -162,7 +164,7 @@ rw_status check_volume(const rw_volume* v, int64_t* nvox, int64_t* batch) {
 // ---------------------------------------------------------------------------
 // Sweep configuration and the autotuner (tile shape, z-chunk, sweeps per graph).
 struct SweepCfg {
-    int tile = 1, tx = 32, ty = 16, nt = 512, zc = 64, ntx = 1, nty = 1, nzc = 1, grid = 1, ipg = 32, waves = 0;
+    int tile = TILE_32x8, tx = 32, ty = 8, nt = 256, zc = 64, ntx = 1, nty = 1, nzc = 1, grid = 1, ipg = 32, waves = 0;
 };
 
 struct Tuned {
@@ -178,9 +180,9 @@ std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     std::vector<int> c;
     (void)gtype;
     if (fp64) {
-        c = {7, 3};
+        c = {TILE_32x8, TILE_40x8};
     } else if (nx <= 24) {
-        c = {7};
+        c = {TILE_32x8};
     } else if (nx <= 48 || (nx % 40 == 0 && nx <= 160)) {
         c = {TILE_S40x20, TILE_S40x8, TILE_R40x20_D2, TILE_R40x20_D3, TILE_R40x8_D2};
     } else {
@@ -594,7 +596,7 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
         ps->cands = {o.tile};  // an explicit tile: its own layout, no tuning
     ps->pad = {0, 0, 0, 0};
     ps->nvec = ntot;
-    if (!fp64 && ps->cands[0] >= TILE_PADDED_FIRST) {
+    if (!fp64 && ps->cands[0] >= TILE_STRIP_FIRST) {
         // padded box: covers whole tiles of every candidate; margins of 2
         // voxels (x: 4 for the strip kernel, whose tiles start 16-byte aligned)
         const int mx = tile_margin(ps->cands[0]);

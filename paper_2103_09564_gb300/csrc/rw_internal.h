@@ -64,7 +64,7 @@ struct SweepArgs {
     const int* list = nullptr;   // optional: the systems to sweep (ascending box indices), else all
     const int* nlist = nullptr;  // length of `list` (device), read by every launch
     int parity;             // index of the (u, p) buffers this launch reads
-    int px, py, pz;         // padded box dims of the streamed vectors (k_sweep4)
+    int px, py, pz;         // padded box dims of the streamed vectors (k_sweep5)
     float c2f;              // -beta * log2(e), FP32 weights
     float wminf;
     double mbeta;           // -beta, FP64 weights
@@ -80,27 +80,30 @@ struct SweepArgs {
 };
 
 enum GType { G_U16 = 0, G_F32 = 1 };
-enum TileId { TILE_32x16 = 1, TILE_64x8 = 2, TILE_40x8 = 3, TILE_40x20 = 4, TILE_80x8 = 5, TILE_80x16 = 6,
-              TILE_32x8 = 7, TILE_32x32 = 8, TILE_64x16 = 9, TILE_W28x28 = 10, TILE_W28x12 = 11, TILE_W28x20 = 12,
-              TILE_W28x28_8W = 13, TILE_P32x12 = 14, TILE_P32x12_D4 = 15, TILE_P32x28 = 16, TILE_P40x20 = 17,
-              TILE_P40x8 = 18, TILE_P32x20 = 19, TILE_S64x11 = 20, TILE_S32x22 = 21, TILE_S32x20 = 22,
-              TILE_S64x8 = 23, TILE_S40x20 = 24, TILE_S40x8 = 25, TILE_T32x20 = 26, TILE_T64x11 = 27,
-              TILE_T32x12 = 28, TILE_T40x20 = 29, TILE_T40x8 = 30, TILE_S32x20_D3 = 31, TILE_S64x8_D3 = 32,
-              TILE_S32x22_D1 = 33, TILE_S64x8_D1 = 34, TILE_S64x14_D1 = 35,
-              // strips of 4 whose p_k and u' are exchanged through the TMA ring slots
-              TILE_R64x14_D2 = 36, TILE_R64x14_D1 = 37, TILE_R64x11_D2 = 38, TILE_R64x11_D3 = 39, TILE_R32x22_D2 = 40, TILE_R32x20_D3 = 41,
-              TILE_R64x13_D3 = 42, TILE_R64x12_D3 = 43,
-              // brick tiles (40-voxel boxes) with the ring exchange
-              TILE_R40x20_D2 = 44, TILE_R40x20_D3 = 45, TILE_R40x8_D2 = 46 };
+// Sweep tiles.  The ids are part of the ABI (RW_TILE_* in rw_api.h); ids
+// missing here are not assigned.
+enum TileId {
+    TILE_40x8 = 3,   // FP64 sweep (k_sweep)
+    TILE_32x8 = 7,   // FP64 sweep, and the FP32 k_sweep2 for boxes narrower than a strip tile
+    // FP32 strip kernel (k_sweep5, strips of 4 voxels), padded layout
+    TILE_S64x11 = 20, TILE_S32x22 = 21, TILE_S32x20 = 22, TILE_S64x8 = 23, TILE_S40x20 = 24, TILE_S40x8 = 25,
+    TILE_S32x20_D3 = 31, TILE_S64x8_D3 = 32, TILE_S32x22_D1 = 33, TILE_S64x8_D1 = 34, TILE_S64x14_D1 = 35,
+    // strips whose p_k and u' are exchanged through the TMA ring slots
+    TILE_R64x14_D2 = 36, TILE_R64x14_D1 = 37, TILE_R64x11_D2 = 38, TILE_R64x11_D3 = 39, TILE_R32x22_D2 = 40,
+    TILE_R32x20_D3 = 41, TILE_R64x13_D3 = 42, TILE_R64x12_D3 = 43,
+    // brick tiles (40-voxel boxes) with the ring exchange
+    TILE_R40x20_D2 = 44, TILE_R40x20_D3 = 45, TILE_R40x8_D2 = 46 };
 constexpr int N_TILES = 47;
 constexpr int TILE_RING_FIRST = TILE_R64x14_D2;  // k_sweep5 with the ring exchange
-constexpr int TILE_PADDED_FIRST = TILE_P32x12;  // tiles from here on use the padded layout (k_sweep4)
-constexpr int TILE_STRIP_FIRST = TILE_S64x11;   // tiles from here on: k_sweep5 (strips of 4, then of 2)
-constexpr int TILE_STRIP2_FIRST = TILE_T32x20;  // k_sweep5 with 2-voxel strips
-// x margin of the padded layout: the strip width of k_sweep5, else 2
-inline int tile_margin(int tile) {
-    return (tile >= TILE_STRIP_FIRST && (tile < TILE_STRIP2_FIRST || tile > TILE_T40x8)) ? 4 : 2;
+constexpr int TILE_STRIP_FIRST = TILE_S64x11;    // tiles from here on: k_sweep5, padded layout
+// Whether a tile id names a compiled sweep of this precision.
+inline bool tile_compiled(int fp64, int tile) {
+    if (fp64) return tile == TILE_40x8 || tile == TILE_32x8;
+    return tile == TILE_32x8 || (tile >= TILE_S64x11 && tile <= TILE_S40x8) ||
+           (tile >= TILE_S32x20_D3 && tile < N_TILES);
 }
+// x margin of the padded layout: the strip width of k_sweep5
+inline int tile_margin(int tile) { return tile >= TILE_STRIP_FIRST ? 4 : 2; }
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
 // combination that is not instantiated.
@@ -143,11 +146,11 @@ int sweep_threads(int tile);
 cudaError_t sweep_prepare(int fp64, int gtype, int tile);  // opt-in dynamic smem
 int sweep_occupancy(int fp64, int gtype, int tile);         // resident CTAs per SM (0: not instantiated)
 
-// Padded layout of the vectors streamed by k_sweep4: a box is [pz][py][px]
-// and user voxel (x, y, z) sits at (x + 2, y + 2, z + 2).  px = 0: unpadded.
+// Padded layout of the vectors streamed by k_sweep5: a box is [pz][py][px]
+// and user voxel (x, y, z) sits at (x + mx, y + 2, z + 2).  px = 0: unpadded.
 struct Pad {
     int px, py, pz;
-    int mx;  // x margin (2, or 4 for the strip kernel); y and z margins are 2
+    int mx;  // x margin (4: the strip width); y and z margins are 2
 };
 
 __host__ __device__ __forceinline__ int64_t vec_index(const Pad& pd, const Boxes& bx, int box, int x, int y,

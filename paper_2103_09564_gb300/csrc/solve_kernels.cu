@@ -15,14 +15,6 @@ cudaError_t sweep2_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s
 cudaError_t sweep2_prepare(int tile);
 int sweep2_occupancy(int tile);
 size_t sweep2_smem(int tile);
-cudaError_t sweep3_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
-cudaError_t sweep3_prepare(int tile);
-int sweep3_occupancy(int tile);
-size_t sweep3_smem(int tile);
-cudaError_t sweep4_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
-cudaError_t sweep4_prepare(int tile);
-int sweep4_occupancy(int tile);
-size_t sweep4_smem(int tile);
 cudaError_t sweep5_launch(int tile, const SweepArgs& a, int grid, cudaStream_t s);
 cudaError_t sweep5_prepare(int tile);
 int sweep5_occupancy(int tile);
@@ -47,7 +39,7 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
                 for (int c = 0; c < N_TILES; ++c) cache[a][b][c] = -1;
         init = true;
     }
-    if (tile < 1 || tile >= N_TILES) return 0;
+    if (!tile_compiled(fp64, tile)) return 0;
     int& slot = cache[fp64 ? 1 : 0][gtype == G_U16 ? 0 : 1][tile];
     if (slot >= 0) return slot;
     if (sweep_prepare(fp64, gtype, tile) != cudaSuccess) {
@@ -56,9 +48,7 @@ int sweep_occupancy(int fp64, int gtype, int tile) {
         return 0;
     }
     if (fp64) slot = gtype == G_U16 ? sweep_occupancy_d64_u16(tile) : sweep_occupancy_d64_f32(tile);
-    else if (tile >= TILE_STRIP_FIRST) slot = sweep5_occupancy(tile);
-    else if (tile >= TILE_PADDED_FIRST) slot = sweep4_occupancy(tile);
-    else slot = tile >= TILE_W28x28 ? sweep3_occupancy(tile) : sweep2_occupancy(tile);
+    else slot = tile >= TILE_STRIP_FIRST ? sweep5_occupancy(tile) : sweep2_occupancy(tile);
     return slot;
 }
 
@@ -86,29 +76,24 @@ int sweep_threads(int tile) {
 }
 
 // FP64 sweeps use the generic kernel (sweep_kernel.cuh); FP32 sweeps the
-// pipelined one (sweep2_kernel.cuh), which reads the packed g|code words.
+// strip kernel (sweep5_kernel.cuh), or for narrow boxes the pipelined one
+// (sweep2_kernel.cuh), which reads packed g|code words.
 size_t sweep_smem_bytes(int fp64, int tile) {
     int tx, ty;
     tile_dims(tile, &tx, &ty);
     const int r2 = (tx + 4) * (ty + 4);
     if (fp64) return (size_t)sweep_planes_bytes<double>(r2);
-    if (tile >= TILE_STRIP_FIRST) return sweep5_smem(tile);
-    if (tile >= TILE_PADDED_FIRST) return sweep4_smem(tile);
-    return tile >= TILE_W28x28 ? sweep3_smem(tile) : sweep2_smem(tile);
+    return tile >= TILE_STRIP_FIRST ? sweep5_smem(tile) : sweep2_smem(tile);
 }
 
 cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int grid, cudaStream_t s) {
     if (fp64) return gtype == G_U16 ? sweep_launch_d64_u16(tile, a, grid, s) : sweep_launch_d64_f32(tile, a, grid, s);
-    if (tile >= TILE_STRIP_FIRST) return sweep5_launch(tile, a, grid, s);
-    if (tile >= TILE_PADDED_FIRST) return sweep4_launch(tile, a, grid, s);
-    return tile >= TILE_W28x28 ? sweep3_launch(tile, a, grid, s) : sweep2_launch(tile, a, grid, s);
+    return tile >= TILE_STRIP_FIRST ? sweep5_launch(tile, a, grid, s) : sweep2_launch(tile, a, grid, s);
 }
 
 cudaError_t sweep_prepare(int fp64, int gtype, int tile) {
     if (fp64) return gtype == G_U16 ? sweep_prepare_d64_u16(tile) : sweep_prepare_d64_f32(tile);
-    if (tile >= TILE_STRIP_FIRST) return sweep5_prepare(tile);
-    if (tile >= TILE_PADDED_FIRST) return sweep4_prepare(tile);
-    return tile >= TILE_W28x28 ? sweep3_prepare(tile) : sweep2_prepare(tile);
+    return tile >= TILE_STRIP_FIRST ? sweep5_prepare(tile) : sweep2_prepare(tile);
 }
 
 // ---------------------------------------------------------------------------

@@ -14,11 +14,6 @@ namespace {
     X(23, 64, 8, 4, 224, 2, 2, false)    \
     X(24, 40, 20, 4, 288, 2, 2, false)   \
     X(25, 40, 8, 4, 160, 2, 3, false)    \
-    X(26, 32, 20, 2, 416, 2, 2, false)   \
-    X(27, 64, 11, 2, 480, 2, 2, false)   \
-    X(28, 32, 12, 2, 288, 2, 3, false)   \
-    X(29, 40, 20, 2, 512, 2, 2, false)   \
-    X(30, 40, 8, 2, 256, 2, 4, false)    \
     X(31, 32, 20, 4, 256, 3, 2, false)   \
     X(32, 64, 8, 4, 224, 3, 2, false)    \
     X(33, 32, 22, 4, 256, 1, 2, false)   \

@@ -1,12 +1,12 @@
 // FP32 fused PCG sweep, register-blocked along x and z.
 //
-// Same iteration as k_sweep4 (single-reduction Jacobi-PCG with explicit
-// A-conjugation, u = D^-1 r stored, weights recomputed from g every sweep,
-// six inner products), organised to spend few instructions per voxel:
+// The iteration of k_sweep (sweep_kernel.cuh: single-reduction Jacobi-PCG
+// with explicit A-conjugation, u = D^-1 r stored, weights recomputed from g
+// every sweep, six inner products), organised to spend few instructions per
+// voxel:
 //
-// * A thread owns a strip of V (4 or 2) consecutive voxels of one row of the
-//   tile (one 16- or 8-byte word of every streamed vector) and marches it
-//   through z.
+// * A thread owns a strip of V = 4 consecutive voxels of one row of the tile
+//   (one 16-byte word of every streamed vector) and marches it through z.
 //   The strip's own values at z-1, z, z+1 (p_k, the g words, the z-edge
 //   weights) stay in registers; only x/y neighbours are exchanged, through
 //   double-buffered shared planes read with vector loads (the strip ends
@@ -49,7 +49,7 @@
 #include <type_traits>
 
 #include "rw_internal.h"
-#include "sweep4_kernel.cuh"
+#include "sweep_kernel.cuh"
 
 namespace rwk {
 

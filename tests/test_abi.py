@@ -72,6 +72,12 @@ def test_invalid_arguments_rejected_on_host(lib):
     v.dims[0] = v.dims[1] = v.dims[2] = 4
     rc = lib.rw_solve(ctypes.byref(v), None, ctypes.byref(o), None, None, ctypes.byref(st), None)
     assert rc == _abi.RW_ERR_INVALID_ARG
+    # tile ids: unassigned values and tiles of the other precision are rejected
+    for tile, prec in ((1, rw.RW_MIXED), (26, rw.RW_MIXED), (_abi.RW_TILE["40x8"], rw.RW_MIXED),
+                       (_abi.RW_TILE["r64x14_d2"], rw.RW_FP64), (47, rw.RW_MIXED)):
+        o = rw.Opts(tile=tile, precision=prec)
+        rc = lib.rw_solve(ctypes.byref(v), None, ctypes.byref(o), None, None, ctypes.byref(st), None)
+        assert rc == _abi.RW_ERR_INVALID_ARG, (tile, prec)
 
 
 def test_new_entry_points_reject_bad_arguments_on_host(lib):

@@ -107,26 +107,20 @@ def test_ill_conditioned_chain_falls_back_to_fp64(rw):
     assert st2["rel_resid"] <= 1e-10
 
 
-@pytest.mark.parametrize("tile", ["32x16", "64x8", "32x8", "32x32", "64x16", "w28x28", "w28x12", "w28x20", "w28x28_8w",
-                                  "p32x12", "p32x12_deep", "p32x28", "p40x20", "p40x8", "p32x20",
-                                  "s64x11", "s32x22", "s32x20", "s64x8", "s40x20", "s40x8", "t32x20", "t64x11",
-                                  "t32x12", "t40x20", "t40x8", "s32x20_d3", "s64x8_d3", "s32x22_d1", "s64x8_d1",
-                                  "s64x14_d1", "r64x14_d2", "r64x14_d1", "r64x11_d2", "r64x11_d3", "r32x22_d2",
-                                  "r32x20_d3", "r64x13_d3", "r64x12_d3", "r40x20_d2", "r40x20_d3", "r40x8_d2"])
+# every FP32 sweep tile (the autotuner's candidates and 32x8, the narrow-box tile)
+STRIP_TILES = ["s64x11", "s32x22", "s32x20", "s64x8", "s40x20", "s40x8", "s32x20_d3", "s64x8_d3", "s32x22_d1",
+               "s64x8_d1", "s64x14_d1", "r64x14_d2", "r64x14_d1", "r64x11_d2", "r64x11_d3", "r32x22_d2",
+               "r32x20_d3", "r64x13_d3", "r64x12_d3", "r40x20_d2", "r40x20_d3", "r40x8_d2"]
+F32_TILES = ["32x8"] + STRIP_TILES
+
+
+@pytest.mark.parametrize("tile", F32_TILES)
 def test_every_u16_tile_matches_oracle(rw, tile):
     c = P.plain_ball(n=48, seed=3)
     xo = _oracle(c, 130.0)
     x, st = _solve(rw, c, beta=130.0, tol=1e-9, tile=tile)
     assert np.max(np.abs(x - xo)) <= TOL
     assert st["tile"] == rw._abi.RW_TILE[tile]
-
-
-F32_TILES = ["32x16", "40x8", "40x20", "80x8", "80x16", "64x8", "32x8", "32x32", "64x16",
-             "w28x28", "w28x12", "w28x20", "w28x28_8w", "p32x12", "p32x12_deep", "p32x28",
-             "p40x20", "p40x8", "p32x20", "s64x11", "s32x22", "s32x20", "s64x8", "s40x20",
-             "s40x8", "t32x20", "t64x11", "t32x12", "t40x20", "t40x8", "s32x20_d3", "s64x8_d3",
-             "s32x22_d1", "s64x8_d1", "s64x14_d1", "r64x14_d2", "r64x14_d1", "r64x11_d2", "r64x11_d3",
-             "r32x22_d2", "r32x20_d3", "r64x13_d3", "r64x12_d3", "r40x20_d2", "r40x20_d3", "r40x8_d2"]
 
 
 @pytest.mark.parametrize("tile", F32_TILES)
@@ -221,8 +215,8 @@ def test_host_pointers_equal_device_pointers(rw):
 
 def test_deterministic(rw):
     c = P.plain_ball(n=40, seed=5)
-    a, _ = _solve(rw, c, beta=130.0, tol=1e-9, tile="32x16")
-    b, _ = _solve(rw, c, beta=130.0, tol=1e-9, tile="32x16")
+    a, _ = _solve(rw, c, beta=130.0, tol=1e-9, tile="r64x14_d2")
+    b, _ = _solve(rw, c, beta=130.0, tol=1e-9, tile="r64x14_d2")
     assert np.array_equal(a, b)
 
 
