@@ -367,13 +367,14 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     bool loop = false;
     int lpar = 0;  // buffer parity of the next looped launch
     // cluster-resident mode (FP32 sweeps in the strip kernels' padded layout,
-    // small boxes): once the active systems fit the resident clusters, the
-    // remaining iterations run there; each system keeps its buffer parity
+    // small boxes): once the active systems are at most kClusterTurns per
+    // resident cluster, the remaining iterations run there; each system keeps
+    // its buffer parity
     const int cl_max = (!fp64 && cfg0.tile >= TILE_STRIP_FIRST && tile_margin(cfg0.tile) == 4)
                            ? cluster_capacity(sa.bx) : 0;
     bool clmode = false;
     auto try_cluster = [&](int n) -> bool {
-        if (cl_max <= 0 || n > cl_max) return false;
+        if (cl_max <= 0 || n > kClusterTurns * cl_max) return false;
         clmode = true;
         return true;
     };
@@ -464,8 +465,8 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
             ca.nx = sa.bx.nx;
             ca.ny = sa.bx.ny;
             ca.nz = sa.bx.nz;
-            ca.pls = (sa.bx.nx * sa.bx.ny + 3) & ~3;
-            ca.nzl = (sa.bx.nz + kClusterSize - 1) / kClusterSize;
+            ca.rs = cluster_row_stride(sa.bx.nx);
+            ca.rows = cluster_rows(sa.bx.ny, sa.bx.nz, kClusterSize);
             ca.sc = sa.sc;
             ca.list = sa.list;
             ca.nlist = sa.nlist;

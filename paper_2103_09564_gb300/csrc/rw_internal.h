@@ -120,6 +120,11 @@ cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int 
 // padded layout (x margin 4, y and z margins 2).
 constexpr int kClusterMaxDim = 40;
 constexpr int kClusterSize = 16;
+// The cluster-resident solver takes over once the active systems are at most
+// kClusterTurns per resident cluster (the clusters take the systems in turn):
+// an iteration of a 40^3 system there costs about 5.6 us, a looped batched
+// iteration of n such systems about 14 + 0.43 n us.
+constexpr int kClusterTurns = 4;
 struct ClusterArgs {
     float* u[2];              // u and p buffers by parity (BoxScalars::par)
     float* p[2];
@@ -127,7 +132,7 @@ struct ClusterArgs {
     const uint32_t* gc;       // signed g words (+g free, -g seed, NaN absent)
     int px, py, pz;           // padded box dims
     int nx, ny, nz;           // box dims
-    int pls, nzl;             // shared-memory plane stride (floats) and planes per CTA
+    int rs, rows;             // shared-memory row stride (floats, cluster_row_stride) and own rows per CTA (cluster_rows)
     BoxScalars* sc;
     const int* list;          // compacted active systems, or nullptr (all, skipping inactive)
     const int* nlist;
@@ -137,6 +142,8 @@ struct ClusterArgs {
     int loop_iters;           // iteration budget per system and launch
     float c2f, wminf;         // weight parameters (as SweepArgs)
 };
+int cluster_row_stride(int nx);
+int cluster_rows(int ny, int nz, int cl);
 size_t cluster_smem_bytes(int nx, int ny, int nz, int cl);
 int cluster_max_active(int nx, int ny, int nz, int cl);
 cudaError_t launch_brick_cluster(const ClusterArgs& a, int nclusters, int cl, cudaStream_t s);

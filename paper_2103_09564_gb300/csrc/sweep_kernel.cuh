@@ -148,10 +148,13 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
     const float e = fmaf(a.hi, b.hi, -p);
     return df_fast(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
 }
+// a / b: a first quotient, the exact remainder a - q1 b in double-FP32, and a
+// correction quotient of the remainder.  The correction absorbs the few ulps
+// of error of the fast FP32 quotients (|b| < 2^126).
 __device__ __forceinline__ DF df_div(DF a, DF b) {
-    const float q1 = a.hi / b.hi;
+    const float q1 = __fdividef(a.hi, b.hi);
     const DF r = df_add(a, df_mul(DF{-q1, 0.0f}, b));
-    return df_fast(q1, r.hi / b.hi);
+    return df_fast(q1, __fdividef(r.hi, b.hi));
 }
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
 __device__ __forceinline__ bool df_pos(DF a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
