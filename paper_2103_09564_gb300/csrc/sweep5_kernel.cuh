@@ -263,8 +263,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
     float* ePF = eUN + 2 * PL;                                   // [2][RY][SX]
     float* ePL = ePF + 2 * PS;                                   // [2][RY][SX]
     float* eUF = ePL + 2 * PS;                                   // [2][RY][SX]
-    __shared__ double red[6 * (NT / 32)];
     __shared__ int s_last;
+    static_assert(6 * NT <= NRU * PLA, "the reduction scratch fits the u ring");
 
     // Threads are ordered by role so that warps are homogeneous: first the
     // strips owning output voxels (rows 0..TY-1, strips 1..TX/V), then the
@@ -554,34 +554,73 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         }
         // the six sums in double-FP32 (FP32 pipes: on GB300 a chain of
         // dependent FP64 operations here would sit on every sweep's critical
-        // path); per-CTA partials are (hi, lo) float pairs in the 8-byte slots
-        const float fv[6] = {a_gam, a_rr, a_del, a_eps, a_pi, a_tau};
-        DF v[6];
-        DF* redf = reinterpret_cast<DF*>(red);
-        block_reduce_df<NT, 6>(fv, v, redf);
-        if (tid == 0) {
-            float2* pp = reinterpret_cast<float2*>(A.partials + ((int64_t)li * tpb + t) * 6);
+        // path).  The per-thread partials go through shared memory (the u ring,
+        // idle between work items: every issued plane has been consumed) and
+        // warp j sums partial j: NT / 32 values per lane in two chains, then a
+        // shuffle tree.  Per-item results are (hi, lo) float pairs in the
+        // 8-byte slots of A.partials.
+        const int lane = tid & 31, wid = tid >> 5;
+        float* rs = rU;  // [6][NT]
+        __syncthreads();  // every thread is done with the ring
+        rs[0 * NT + tid] = a_gam;
+        rs[1 * NT + tid] = a_rr;
+        rs[2 * NT + tid] = a_del;
+        rs[3 * NT + tid] = a_eps;
+        rs[4 * NT + tid] = a_pi;
+        rs[5 * NT + tid] = a_tau;
+        __syncthreads();
+        if (wid < 6) {
+            const float* r = rs + wid * NT;
+            DF c0 = {0.0f, 0.0f}, c1 = {0.0f, 0.0f};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) pp[k] = make_float2(v[k].hi, v[k].lo);
-            __threadfence();
+            for (int i = 0; i < NT / 32; i += 2) {
+                c0 = df_add(c0, DF{r[lane + 32 * i], 0.0f});
+                if (i + 1 < NT / 32) c1 = df_add(c1, DF{r[lane + 32 * i + 32], 0.0f});
+            }
+            DF v = df_add(c0, c1);
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) v = df_add(v, df_shfl_xor(v, m));
+            if (lane == 0) {
+                float2* pp = reinterpret_cast<float2*>(A.partials + ((int64_t)li * tpb + t) * 6);
+                pp[wid] = make_float2(v.hi, v.lo);
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
             const unsigned prev = atomicAdd(&S->counter, 1u);
             s_last = (prev == (unsigned)tpb - 1u);
         }
         __syncthreads();
         if (s_last) {
             __threadfence();
-            DF tv[6];
-#pragma unroll
-            for (int j = 0; j < 6; ++j) tv[j] = DF{0.0f, 0.0f};
-            const float2* pb = reinterpret_cast<const float2*>(A.partials + (int64_t)li * tpb * 6);
-            for (int k = tid; k < tpb; k += NT)
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    const float2 q = __ldcg(pb + 6 * k + j);
-                    tv[j] = df_add(tv[j], DF{q.x, q.y});
+            DF* tot = reinterpret_cast<DF*>(rs);  // [6], after the reads of rs below
+            DF v = {0.0f, 0.0f};
+            if (wid < 6) {
+                // warp j: partial j of the tpb work items of the system
+                const float2* pb = reinterpret_cast<const float2*>(A.partials + (int64_t)li * tpb * 6) + wid;
+                DF c0 = {0.0f, 0.0f}, c1 = {0.0f, 0.0f};
+                int k = lane;
+                for (; k + 32 < tpb; k += 64) {
+                    const float2 q0 = __ldcg(pb + 6 * k), q1 = __ldcg(pb + 6 * (k + 32));
+                    c0 = df_add(c0, DF{q0.x, q0.y});
+                    c1 = df_add(c1, DF{q1.x, q1.y});
                 }
-            block_reduce_df2<NT, 6>(tv, redf);
+                if (k < tpb) {
+                    const float2 q0 = __ldcg(pb + 6 * k);
+                    c0 = df_add(c0, DF{q0.x, q0.y});
+                }
+                v = df_add(c0, c1);
+#pragma unroll
+                for (int m = 16; m > 0; m >>= 1) v = df_add(v, df_shfl_xor(v, m));
+            }
+            __syncthreads();  // rs is read no more
+            if (wid < 6 && lane == 0) tot[wid] = v;
+            __syncthreads();
             if (tid == 0) {
+                DF tv[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) tv[j] = tot[j];
                 if constexpr (LOOP) {
                     // the record as other CTAs left it, updated in registers
                     BoxScalars loc;

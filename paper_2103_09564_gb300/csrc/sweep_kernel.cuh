@@ -168,58 +168,6 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int m) {
     return DF{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
 }
 
-// Block-wide double-FP32 sums of NV per-thread FP32 values: each warp's 32
-// lanes in a shuffle tree, then the warp sums in a tree of warp 0.  The
-// result is valid in thread 0.  red: NV * (NT / 32) DF values.
-template <int NT, int NV>
-__device__ __forceinline__ void block_reduce_df(const float* f, DF* v, DF* red) {
-    constexpr int NW = NT / 32;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = DF{f[k], 0.0f};
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[k * NW + wid] = v[k];
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = lane < NW ? red[k * NW + lane] : DF{0.0f, 0.0f};
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
-    }
-    __syncthreads();
-}
-
-// Same for per-thread double-FP32 values.
-template <int NT, int NV>
-__device__ __forceinline__ void block_reduce_df2(DF* v, DF* red) {
-    constexpr int NW = NT / 32;
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[k * NW + wid] = v[k];
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = lane < NW ? red[k * NW + lane] : DF{0.0f, 0.0f};
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) v[k] = df_add(v[k], df_shfl_xor(v[k], m));
-    }
-    __syncthreads();
-}
-
 // finalize_box (below) in double-FP32: the same recurrences and decisions on
 // the six sums of a sweep, without a chain of dependent FP64 operations (the
 // record keeps FP64 fields; they are converted on the way in and out).
