@@ -136,10 +136,8 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
     const int tx = tid % NX, trow = tid / NX;
     const bool tlive = trow < RPI;
     // padded layout: x margin 4, y and z margins 2, margins absent
-    auto gidx = [&](int64_t gbase, int R) -> int64_t {
-        const int z = R >= 0 ? R / NY : -1, y = R - z * NY;  // R >= -NY
-        return gbase + (int64_t)(z + 2) * plane_g + (int64_t)(y + 2) * A.px + (tx + 4);
-    };
+    // the strip kernel's layout (no margins, rows of A.px >= NX voxels): system row R = z NY + y
+    auto gidx = [&](int64_t gbase, int R) -> int64_t { return gbase + (int64_t)R * A.px + tx; };
 
     for (int li = (int)cl_id(); li < nlist; li += (int)cl_count()) {
         const int box = A.list ? A.list[li] : li;
@@ -170,38 +168,52 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
         // zero everything (padding columns and unwritten ghost slots stay 0)
         for (int i = tid; i < n_smem; i += kClNT) P[i] = 0.0f;
         __syncthreads();
-        // own rows: state, forward weights, diagonal
-        for (int j = tlive ? trow : nown; j < nown; j += RPI) {
-            const int64_t gi = gidx(gbase, r0 + j);
-            const int o = j * RS + tx, l = (j + NY) * RS + tx;
-            U[o] = __ldcg(ug + gi);
-            P[l] = __ldcg(pg + gi);
-            X[o] = __ldcg(xg + gi);
-            const uint32_t g0 = gg[gi];
-            const float wR = wgt5(g0, gg[gi + 1], A.c2f, A.wminf);
-            const float wD = wgt5(g0, gg[gi + A.px], A.c2f, A.wminf);
-            const float wF = wgt5(g0, gg[gi + plane_g], A.c2f, A.wminf);
-            const float wL = wgt5(gg[gi - 1], g0, A.c2f, A.wminf);
-            const float wU = wgt5(gg[gi - A.px], g0, A.c2f, A.wminf);
-            const float wB = wgt5(gg[gi - plane_g], g0, A.c2f, A.wminf);
-            WX[o] = wR;
-            WY[l] = wD;
-            WZ[l] = wF;
-            const float d = ((wL + wR) + (wU + wD)) + (wB + wF);
-            Dg[o] = ((int)g0 >= 0 && d > 0.0f) ? d : 0.0f;  // free voxels carry +g
+        // own rows: state, forward weights, diagonal (neighbours beyond the box are absent)
+        {
+            int y = (r0 + trow) % NY, z = (r0 + trow) / NY;
+            for (int j = tlive ? trow : nown; j < nown; j += RPI, y += RPI) {
+                while (y >= NY) y -= NY, ++z;
+                const int64_t gi = gidx(gbase, r0 + j);
+                const int o = j * RS + tx, l = (j + NY) * RS + tx;
+                U[o] = __ldcg(ug + gi);
+                P[l] = __ldcg(pg + gi);
+                X[o] = __ldcg(xg + gi);
+                const uint32_t g0 = gg[gi];
+                const uint32_t gR = tx + 1 < A.px ? gg[gi + 1] : GC_ABSENT, gL = tx > 0 ? gg[gi - 1] : GC_ABSENT;
+                const uint32_t gD = y + 1 < NY ? gg[gi + A.px] : GC_ABSENT, gU = y > 0 ? gg[gi - A.px] : GC_ABSENT;
+                const uint32_t gF = z + 1 < NZ ? gg[gi + plane_g] : GC_ABSENT, gB = z > 0 ? gg[gi - plane_g] : GC_ABSENT;
+                const float wR = wgt5(g0, gR, A.c2f, A.wminf);
+                const float wD = wgt5(g0, gD, A.c2f, A.wminf);
+                const float wF = wgt5(g0, gF, A.c2f, A.wminf);
+                const float wL = wgt5(gL, g0, A.c2f, A.wminf);
+                const float wU = wgt5(gU, g0, A.c2f, A.wminf);
+                const float wB = wgt5(gB, g0, A.c2f, A.wminf);
+                WX[o] = wR;
+                WY[l] = wD;
+                WZ[l] = wF;
+                const float d = ((wL + wR) + (wU + wD)) + (wB + wF);
+                Dg[o] = ((int)g0 >= 0 && d > 0.0f) ? d : 0.0f;  // free voxels carry +g
+            }
         }
-        // ghost rows: u (both parity slots), p, and the forward y / z weights of the lower ones
+        // ghost rows inside the system: u (both parity slots), p, and the
+        // forward y / z weights of the lower ones (rows beyond the system stay 0)
         for (int j = tlive ? trow : NY; j < NY; j += RPI) {
             const int o = j * RS + tx;
-            const int64_t glo = gidx(gbase, r0 - NY + j), ghi = gidx(gbase, r1 + j);
-            const float ulo = __ldcg(ug + glo), uhi = __ldcg(ug + ghi);
-            UG[o] = UG[2 * G + o] = ulo;
-            UG[G + o] = UG[3 * G + o] = uhi;
-            P[o] = __ldcg(pg + glo);
-            P[(NY + nown) * RS + o] = __ldcg(pg + ghi);
-            const uint32_t g0 = gg[glo];
-            WY[o] = wgt5(g0, gg[glo + A.px], A.c2f, A.wminf);
-            WZ[o] = wgt5(g0, gg[glo + plane_g], A.c2f, A.wminf);
+            const int rlo = r0 - NY + j, rhi = r1 + j;
+            if (rlo >= 0) {
+                const int64_t glo = gidx(gbase, rlo);
+                const int y = rlo % NY;
+                UG[o] = UG[2 * G + o] = __ldcg(ug + glo);
+                P[o] = __ldcg(pg + glo);
+                const uint32_t g0 = gg[glo];
+                WY[o] = wgt5(g0, y + 1 < NY ? gg[glo + A.px] : GC_ABSENT, A.c2f, A.wminf);
+                WZ[o] = wgt5(g0, gg[glo + plane_g], A.c2f, A.wminf);  // rlo + NY < NR: own row
+            }
+            if (rhi < NR) {
+                const int64_t ghi = gidx(gbase, rhi);
+                UG[G + o] = UG[3 * G + o] = __ldcg(ug + ghi);
+                P[(NY + nown) * RS + o] = __ldcg(pg + ghi);
+            }
         }
         cl_sync();  // set up everywhere before any remote write
 

@@ -282,22 +282,26 @@ rw_status strip_maps(int tile, SweepArgs* sa, bool loop = false) {
     int tx, ty;
     tile_dims(tile, &tx, &ty);
     const int v = tile_margin(tile);
-    const cuuint64_t gdim[3] = {(cuuint64_t)sa->px, (cuuint64_t)sa->py, (cuuint64_t)sa->pz * (cuuint64_t)sa->bx.nbox};
-    const cuuint64_t gstr[2] = {(cuuint64_t)sa->px * 4, (cuuint64_t)sa->px * (cuuint64_t)sa->py * 4};
-    const cuuint32_t box_t[3] = {(cuuint32_t)(tx + 2 * v), (cuuint32_t)(ty + 3), 1u};
+    // 4-D maps (x, y, z, box): a load that reaches beyond a box on any face
+    // is filled, with zeros (u, p, delta) or NaN (the g words: absent voxels)
+    const cuuint64_t gdim[4] = {(cuuint64_t)sa->px, (cuuint64_t)sa->py, (cuuint64_t)sa->pz, (cuuint64_t)sa->bx.nbox};
+    const cuuint64_t gstr[3] = {(cuuint64_t)sa->px * 4, (cuuint64_t)sa->px * (cuuint64_t)sa->py * 4,
+                                (cuuint64_t)sa->px * (cuuint64_t)sa->py * (cuuint64_t)sa->pz * 4};
+    const cuuint32_t box_t[4] = {(cuuint32_t)(tx + 2 * v), (cuuint32_t)(ty + 3), 1u, 1u};
     // delta: the interior for 4-voxel strips, the full strip width for 2-voxel
     // strips (whose interior does not start 16-byte aligned)
-    const cuuint32_t box_x[3] = {(cuuint32_t)(v == 4 ? tx : tx + 2 * v), (cuuint32_t)ty, 1u};
-    const cuuint32_t es[3] = {1u, 1u, 1u};
-    auto enc = [&](CUtensorMap* m, const void* ptr, const cuuint32_t* box) {
-        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr), gdim, gstr, box, es,
+    const cuuint32_t box_x[4] = {(cuuint32_t)(v == 4 ? tx : tx + 2 * v), (cuuint32_t)ty, 1u, 1u};
+    const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+    auto enc = [&](CUtensorMap* m, const void* ptr, const cuuint32_t* box, bool nan_fill = false) {
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(ptr), gdim, gstr, box, es,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                      nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
     };
-    if (!enc(&sa->tm.u, sa->u_in, box_t) || !enc(&sa->tm.p, sa->p_in, box_t) || !enc(&sa->tm.g, sa->gc, box_t) ||
+    if (!enc(&sa->tm.u, sa->u_in, box_t) || !enc(&sa->tm.p, sa->p_in, box_t) || !enc(&sa->tm.g, sa->gc, box_t, true) ||
         !enc(&sa->tm.x, sa->x, box_x) ||
         (loop && (!enc(&sa->tm.ua, sa->u_out, box_t) || !enc(&sa->tm.pa, sa->p_out, box_t))))
-        return fail(RW_ERR_CUDA, "TMA descriptor encoding failed (tile %d, padded %d x %d x %d)", tile, sa->px, sa->py,
+        return fail(RW_ERR_CUDA, "TMA descriptor encoding failed (tile %d, box %d x %d x %d)", tile, sa->px, sa->py,
                     sa->pz);
     return RW_OK;
 }
@@ -573,7 +577,7 @@ rw_status time_tile(DevWorkspace* w, const SweepCfg& cfg, SweepArgs sa, void* co
 // (autotuned once per problem class), partial-sum storage.
 struct PrecState {
     int fp64 = 0;
-    Pad pad = {0, 0, 0, 0};   // layout of u, p, delta, g|code for this precision
+    Pad pad = {};          // layout of u, p, delta, g|code for this precision
     int64_t nvec = 0;      // elements of each streamed vector
     void* u[2] = {nullptr, nullptr};
     void* p[2] = {nullptr, nullptr};
@@ -595,23 +599,13 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     if (ps->cands.empty()) return fail(RW_ERR_INVALID_ARG, "no sweep kernel for this precision/storage");
     if (o.tile != RW_TILE_AUTO && sweep_occupancy(fp64, P.gtype, o.tile) > 0)
         ps->cands = {o.tile};  // an explicit tile: its own layout, no tuning
-    ps->pad = {0, 0, 0, 0};
+    ps->pad = {};
     ps->nvec = ntot;
     if (!fp64 && ps->cands[0] >= TILE_STRIP_FIRST) {
-        // padded box: covers whole tiles of every candidate; margins of 2
-        // voxels (x: 4 for the strip kernel, whose tiles start 16-byte aligned)
-        const int mx = tile_margin(ps->cands[0]);
-        int px = 0, py = 0;
-        for (int t : ps->cands) {
-            int tx, ty;
-            tile_dims(t, &tx, &ty);
-            px = std::max(px, tx * ((bx.nx + tx - 1) / tx));
-            py = std::max(py, ty * ((bx.ny + ty - 1) / ty));
-        }
-        ps->pad.mx = mx;
-        ps->pad.px = ((px + 2 * mx) + 3) & ~3;
-        ps->pad.py = py + 4;
-        ps->pad.pz = bx.nz + 4;
+        // the strip kernel's layout: no margins, rows of a multiple of 4 voxels
+        ps->pad.px = (bx.nx + 3) & ~3;
+        ps->pad.py = bx.ny;
+        ps->pad.pz = bx.nz;
         ps->nvec = (int64_t)ps->pad.px * ps->pad.py * ps->pad.pz * bx.nbox;
     }
     RCK(ws_get(w, S_U0, ps->nvec * tsz, &ps->u[0]));
@@ -619,7 +613,7 @@ rw_status prec_setup(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, i
     RCK(ws_get(w, S_P0, ps->nvec * tsz, &ps->p[0]));
     RCK(ws_get(w, S_P1, ps->nvec * tsz, &ps->p[1]));
     if (ps->pad.px) {
-        // the margins must read as absent voxels with zero vectors
+        // the columns beyond nx must read as absent voxels with zero vectors
         for (int k = 0; k < 2; ++k) {
             CK(cudaMemsetAsync(ps->u[k], 0, ps->nvec * tsz, w->stream));
             CK(cudaMemsetAsync(ps->p[k], 0, ps->nvec * tsz, w->stream));

@@ -64,7 +64,7 @@ struct SweepArgs {
     const int* list = nullptr;   // optional: the systems to sweep (ascending box indices), else all
     const int* nlist = nullptr;  // length of `list` (device), read by every launch
     int parity;             // index of the (u, p) buffers this launch reads
-    int px, py, pz;         // padded box dims of the streamed vectors (k_sweep5)
+    int px, py, pz;         // box dims of the streamed vectors (k_sweep5: Pad of the strip layout)
     float c2f;              // -beta * log2(e), FP32 weights
     float wminf;
     double mbeta;           // -beta, FP64 weights
@@ -130,7 +130,7 @@ struct ClusterArgs {
     float* p[2];
     float* x;                 // FP32 correction delta
     const uint32_t* gc;       // signed g words (+g free, -g seed, NaN absent)
-    int px, py, pz;           // padded box dims
+    int px, py, pz;           // box dims of the streamed vectors (the strip kernel's layout)
     int nx, ny, nz;           // box dims
     int rs, rows;             // shared-memory row stride (floats, cluster_row_stride) and own rows per CTA (cluster_rows)
     BoxScalars* sc;
@@ -153,17 +153,21 @@ int sweep_threads(int tile);
 cudaError_t sweep_prepare(int fp64, int gtype, int tile);  // opt-in dynamic smem
 int sweep_occupancy(int fp64, int gtype, int tile);         // resident CTAs per SM (0: not instantiated)
 
-// Padded layout of the vectors streamed by k_sweep5: a box is [pz][py][px]
-// and user voxel (x, y, z) sits at (x + mx, y + 2, z + 2).  px = 0: unpadded.
+// Layout of the vectors streamed by k_sweep5 (px != 0): a box is [pz][py][px]
+// and user voxel (x, y, z) sits at (x + mx, y + my, z + mz).  The strip
+// kernel's layout has no margins (its TMA loads fill everything outside the
+// box: zeros for u, p and delta, NaN -- absent -- for the g words) and px = nx
+// rounded up to a multiple of 4 (16-byte rows; the extra columns are absent
+// voxels).  px = 0: the unpadded caller layout.
 struct Pad {
     int px, py, pz;
-    int mx;  // x margin (4: the strip width); y and z margins are 2
+    int mx, my, mz;
 };
 
 __host__ __device__ __forceinline__ int64_t vec_index(const Pad& pd, const Boxes& bx, int box, int x, int y,
                                                       int z) {
     if (pd.px == 0) return (((int64_t)box * bx.nz + z) * bx.ny + y) * bx.nx + x;
-    return (((int64_t)box * pd.pz + (z + 2)) * pd.py + (y + 2)) * pd.px + (x + pd.mx);
+    return (((int64_t)box * pd.pz + (z + pd.mz)) * pd.py + (y + pd.my)) * pd.px + (x + pd.mx);
 }
 
 // (x, y, z) of the linear index li of an nx * ny * nz box: 32-bit division

@@ -193,7 +193,7 @@ extern "C" rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* 
     // clear what must start at zero
     NCK(cudaMemsetAsync(sc, 0, batch * sizeof(BoxScalars), s));
     NCK(launch_quantize(vol->data, vol->dtype, ntot, vol->lo, vol->hi, vol->normalize, RW_STORE_UNORM16, g, s));
-    NCK(launch_pack_gc(bx, Pad{0, 0, 0, 0}, g, G_U16, seeds->code, gc, s));
+    NCK(launch_pack_gc(bx, Pad{}, g, G_U16, seeds->code, gc, s));
     ResidArgs ra{};
     ra.bx = bx;
     ra.g = g;
@@ -263,7 +263,7 @@ extern "C" rw_status rw_solve_noalloc(const rw_volume* vol, const rw_seed_mask* 
             NCK(cudaMemcpyAsync(&n_act, nact, sizeof(int), cudaMemcpyDeviceToHost, s));
             NCK(cudaStreamSynchronize(s));
         }
-        NCK(launch_accumulate(bx, Pad{0, 0, 0, 0}, seeds->code, delta, xhi, s));
+        NCK(launch_accumulate(bx, Pad{}, seeds->code, delta, xhi, s));
         ra.keep_p = 1;
         NCK(launch_residual(0, ra, delta, s));
         NCK(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, s));

@@ -41,9 +41,11 @@
 // Tile: TX x TY interior voxels (TX a multiple of V).  The thread grid covers
 // strips x = -V .. TX+V-1 (SX = TX/V + 2 strips) and rows y = -1 .. TY+1
 // (RY = TY + 3 rows): p_k is needed on x = -1 .. TX+1, y = -1 .. TY+1; u' on
-// x = 0 .. TX, y = 0 .. TY (the +x / +y ends of the owned edges).  This needs
-// the padded layout with an x margin of V voxels (the first strip of a tile
-// starts 4V-byte aligned) and y / z margins of 2, margins absent (NaN).
+// x = 0 .. TX, y = 0 .. TY (the +x / +y ends of the owned edges).  The
+// vectors have no margins: the 4-D tensor maps (x, y, z, box) fill what a
+// tile copy reads beyond the box with zeros (u, p, delta) or NaN (g: absent
+// voxels), and strips beyond the box do not store.  Rows are padded to a
+// multiple of V voxels (16-byte TMA rows and strip starts).
 #pragma once
 
 #include <type_traits>
@@ -139,11 +141,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
-__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
-            "r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
 
@@ -341,8 +344,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         const int z1 = min(z0 + A.zc, ez);
         float a_gam = 0.f, a_rr = 0.f, a_del = 0.f, a_eps = 0.f, a_pi = 0.f, a_tau = 0.f;
         if (z0 < ez) {
-            // padded coordinates of this strip: x + V, y + 2, z + 2
-            const int64_t base = (int64_t)box * bstride + (int64_t)(ty * TY + ry + 1) * PX + tx * TX + V * sx;
+            // this strip's first voxel (inner strips: x = tx TX + V (sx - 1), y = ty TY + ry - 1);
+            // strips beyond the box (a tile's ragged edge) do not store
+            const int gx = tx * TX + V * (sx - 1), gy = ty * TY + ry - 1;
+            const bool in_box = gx < PX && gy < PY;
+            const int64_t base = (int64_t)box * bstride + (int64_t)gy * PX + gx;
             float* Xb = static_cast<float*>(A.x) + base;
             float* Uo = u_out + base;
             float* Po = p_out + base;
@@ -356,9 +362,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             auto slotg = [&](int z) { return (int)((q0 + (uint32_t)z) % NRG); };
             auto phase = [&](int z) { return ((q0 + (uint32_t)z) / NRU) & 1u; };
             // TMA box origins: the tile's first strip and row (x = -V, y = -1)
-            // for u, p, g; row y = 0 from column x = XC - V for delta
-            const int cx = tx * TX, cy = ty * TY + 1;
-            const int cz = box * A.pz + 2;
+            // for u, p, g; row y = 0 from column x = XC - V for delta; the
+            // 4th coordinate is the box
+            const int cx = tx * TX - V, cy = ty * TY - 1;
             auto issue = [&](int z) {
                 if (tid != 0) return;
                 const int sl = slot(z), su = slotu(z);
@@ -366,10 +372,10 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 const bool wx = z >= z0 && z < z1;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_expect_tx(bar, (uint32_t)(3 * PL * 4 + (wx ? XW * TY * 4 : 0)));
-                tma_load3(sU + su * PLA * 4, mu, cx, cy, cz + z, bar);
-                tma_load3(sP + sl * PLA * 4, mp, cx, cy, cz + z, bar);
-                tma_load3(sG + slotg(z) * PLA * 4, &A.tm.g, cx, cy, cz + z, bar);
-                if (wx) tma_load3(sX + sl * NIA * 4, &A.tm.x, cx + XC, cy + 1, cz + z, bar);
+                tma_load4(sU + su * PLA * 4, mu, cx, cy, z, box, bar);
+                tma_load4(sP + sl * PLA * 4, mp, cx, cy, z, box, bar);
+                tma_load4(sG + slotg(z) * PLA * 4, &A.tm.g, cx, cy, z, box, bar);
+                if (wx) tma_load4(sX + sl * NIA * 4, &A.tm.x, cx + XC, cy + 1, z, box, bar);
             };
 
             // One plane step.  At entry `in` holds the strip's registers for
@@ -455,14 +461,16 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                         eUF[BC * PS + sofs] = un0[0];
                     }
                     if (inner && z < z1) {
-                        const int64_t pz = (int64_t)(z + 2) * plane;
+                        const int64_t pz = (int64_t)z * plane;
                         float xn[V];
                         ldv<V>(rX + slot(z) * NIA + xofs, xn);
 #pragma unroll
                         for (int i = 0; i < V; ++i) xn[i] = fmaf(alpha, in.pk0[i], xn[i]);
-                        stv<V>(Uo + pz, un0);
-                        stv<V>(Po + pz, in.pk0);
-                        stv<V>(Xb + pz, xn);
+                        if (in_box) {
+                            stv<V>(Uo + pz, un0);
+                            stv<V>(Po + pz, in.pk0);
+                            stv<V>(Xb + pz, xn);
+                        }
 #pragma unroll
                         for (int i = 0; i < V; ++i) {
                             // p_k and u' vanish on non-free voxels
@@ -569,8 +577,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         rs[4 * NT + tid] = a_pi;
         rs[5 * NT + tid] = a_tau;
         __syncthreads();
-        if (wid < 6) {
-            const float* r = rs + wid * NT;
+        // (fewer than six warps: warp w also takes partials w + NT / 32, ...)
+        for (int j = wid; j < 6; j += NT / 32) {
+            const float* r = rs + j * NT;
             DF c0 = {0.0f, 0.0f}, c1 = {0.0f, 0.0f};
 #pragma unroll
             for (int i = 0; i < NT / 32; i += 2) {
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
             for (int m = 16; m > 0; m >>= 1) v = df_add(v, df_shfl_xor(v, m));
             if (lane == 0) {
                 float2* pp = reinterpret_cast<float2*>(A.partials + ((int64_t)li * tpb + t) * 6);
-                pp[wid] = make_float2(v.hi, v.lo);
+                pp[j] = make_float2(v.hi, v.lo);
                 __threadfence();
             }
         }
@@ -594,11 +603,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
         __syncthreads();
         if (s_last) {
             __threadfence();
-            DF* tot = reinterpret_cast<DF*>(rs);  // [6], after the reads of rs below
-            DF v = {0.0f, 0.0f};
-            if (wid < 6) {
-                // warp j: partial j of the tpb work items of the system
-                const float2* pb = reinterpret_cast<const float2*>(A.partials + (int64_t)li * tpb * 6) + wid;
+            DF* tot = reinterpret_cast<DF*>(rs);  // [6]
+            for (int j = wid; j < 6; j += NT / 32) {
+                // warp w: partial j of the tpb work items of the system
+                DF v;
+                const float2* pb = reinterpret_cast<const float2*>(A.partials + (int64_t)li * tpb * 6) + j;
                 DF c0 = {0.0f, 0.0f}, c1 = {0.0f, 0.0f};
                 int k = lane;
                 for (; k + 32 < tpb; k += 64) {
@@ -613,9 +622,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
                 v = df_add(c0, c1);
 #pragma unroll
                 for (int m = 16; m > 0; m >>= 1) v = df_add(v, df_shfl_xor(v, m));
+                if (lane == 0) tot[j] = v;  // rs is read no more: the items' sums are in A.partials
             }
-            __syncthreads();  // rs is read no more
-            if (wid < 6 && lane == 0) tot[wid] = v;
             __syncthreads();
             if (tid == 0) {
                 DF tv[6];
