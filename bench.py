@@ -14,7 +14,7 @@ hierarchical 1024^3 vessel-tree workload (brick 32) with its roofline and the
 batched mixed-precision vs per-brick FP64 comparison on its own leaf level.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload plain|hier|adjoint|multiclass]
+                  [--workload plain|hier|adjoint|multiclass|bricks]
 
 --impl reference times the FP64 CPU oracle (test infrastructure, as it
 stands) on the host cores: each step is a bounded number of its PCG
@@ -44,15 +44,15 @@ TOL = 1e-8
 SWEEP_BYTES_PER_VOXEL = 27
 KERNEL_BYTES_PER_VOXEL = 28
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sweep5
-# launch on the 256^3 workload, per tile: median over an ncu launch list of
-# `bench.py --steps 1 --warmup 3` (autotuning sweeps included).  Valid only
-# for the strip-sweep sources they were measured on (SHA-256 of the files
-# below, first 16 hex digits); any other source gives traffic null.
-SWEEP_SOURCES = ("paper_2103_09564_gb300/csrc/sweep5_kernel.cuh", "paper_2103_09564_gb300/csrc/sweep5_f32.cu")
-SWEEP_TRAFFIC_256 = {"sha": "66972cfa6d102de5",
-                     "bytes": {"s32x20_d3": 457.2e6, "s32x20": 460.1e6, "s64x8": 455.4e6, "s64x8_d3": 454.5e6,
-                               "s32x22_d1": 471.9e6, "s64x8_d1": 462.9e6, "s32x22": 469.8e6, "s64x11": 472.8e6,
-                               "s64x14_d1": 482.5e6}}
+# launch on the 256^3 workload, per tile, from one ncu capture of that tile
+# (`ncu --set full -k regex:k_sweep5 -s 40 -c 1` over `bench.py --steps 2
+# --warmup 3 --no-cpu-baseline --no-oracle-check --no-secondary --e2e-steps 0
+# --tile <tile>`).  Valid only for the sweep sources they were measured on
+# (SHA-256 of the files below, first 16 hex digits); any other source, or a
+# tile without a capture, gives traffic null.
+SWEEP_SOURCES = ("paper_2103_09564_gb300/csrc/sweep5_kernel.cuh", "paper_2103_09564_gb300/csrc/sweep5_f32.cu",
+                 "paper_2103_09564_gb300/csrc/sweep_kernel.cuh")
+SWEEP_TRAFFIC_256 = {"sha": "914c99994bcc7339", "bytes": {"r64x14_d2": 432.35e6}}
 
 
 def _sweep_source_sha():
@@ -525,6 +525,54 @@ def run_hier(args):
     return 0
 
 
+def run_bricks(args):
+    """Batched brick solves, the unit of work of a hierarchy level: n systems
+    (default 200) of 40^3 voxels (brick 32 with its 1.25 neighbourhood), each
+    a noisy ball or ellipsoid (phantoms.ball_case, seeds 0..n-1), beta 130,
+    solved together to tol (default 1e-10).  One step = one batched solve:
+    full-batch sweeps, then looped sweeps and the cluster-resident solver as
+    the systems converge."""
+    import torch
+    import paper_2103_09564_gb300 as rw
+    import phantoms as P
+    nb = args.n or 200
+    cs = [P.ball_case(n=40, seed=s, radius=10.0 + (s % 5), ellipsoid=(s % 2 == 1)) for s in range(nb)]
+    dev = torch.device("cuda", 0)
+    vol, code, val = (torch.from_numpy(np.stack([c[k] for c in cs])).to(dev) for k in ("volume", "code", "value"))
+    opts = rw.Opts(beta=BETA, tol=args.tol, tile=args.tile)
+    for _ in range(max(3, args.warmup)):
+        rw.rw_solve(vol, code, val, opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            stats.append(rw.rw_solve(vol, code, val, opts)[1])
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    vi = sum(st["voxel_iters"] for st in stats)
+    sweep_ms = sum(st["ms_sweeps"] for st in stats)
+    peak, src = _peaks()
+    eff = SWEEP_BYTES_PER_VOXEL * vi / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+    tile_name = {v: k for k, v in rw._abi.RW_TILE.items()}.get(stats[0]["tile"], str(stats[0]["tile"]))
+    line = {"metric": METRIC, "value": vi / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched brick solves, {nb} systems of 40^3 (phantoms.ball_case, seeds 0..{nb - 1}), "
+                                   f"beta {BETA}, tol {args.tol}",
+                       "iters": stats[0]["iters"], "sweeps": stats[0]["sweeps"], "tile": tile_name,
+                       "free_voxels": stats[0]["free_voxels"], "rel_resid": stats[0]["rel_resid"]},
+            "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s",
+                         "frac": (eff / peak) if eff else None, "traffic": None,
+                         "kernel": "fused PCG sweeps over the brick batch (device time of the sweeps)",
+                         "basis": "27 B per free-voxel iteration", "peak_source": src},
+            "gpu_launches": int(sum(st["launches"] for st in stats)), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _compare_batched_vs_fp64(rw, P, s, tol):
     ph = P.vessel_tree(n=256, seed=1, n_segments=60)
     xyz, val = _labels_np(ph)
@@ -722,7 +770,7 @@ def main():
                     help="skip the hierarchical 1024^3 workload reported beside the headline")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", default="auto", help="sweep tile (default: autotuned)")
-    ap.add_argument("--workload", default="plain", choices=["plain", "hier", "adjoint", "multiclass"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "hier", "adjoint", "multiclass", "bricks"],
                     help="plain: the 256^3 headline workload; hier: hierarchical 1024^3 vessel tree; "
                          "adjoint: 32 x 96^3 differentiable batch; multiclass: incremental 3-class "
                          "hierarchy on 1024 x 1024 x 2048")
@@ -740,6 +788,8 @@ def main():
         return run_reference(args)
     if args.workload == "hier":
         return run_hier(args)
+    if args.workload == "bricks":
+        return run_bricks(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
     if args.workload == "multiclass":

@@ -135,6 +135,21 @@ def test_every_f32_tile_matches_oracle(rw, tile, beta, bound):
     assert np.max(np.abs(x - xo)) <= bound
 
 
+def test_every_strip_tile_takes_the_same_iterations(rw):
+    # the tiles differ only in how the sweep is cut into work items: the six
+    # sums of every sweep must be the same up to rounding, so that each exact
+    # line step leaves (D u', p_k) at rounding level and every tile needs the
+    # same iterations (a tile whose per-item sums lost a term took 60 % more)
+    c = P.random_case((9, 40, 41), seed=6, seed_frac=0.05, beta=25.0)
+    its = {}
+    for tile in STRIP_TILES:
+        x, st = _solve(rw, c, beta=25.0, tol=1e-10, tile=tile)
+        assert st["fp64_fallbacks"] == 0 and st["rel_resid"] <= 1e-10, tile
+        its[tile] = st["iters"]
+    ref = its["s40x20"]
+    assert all(abs(v - ref) <= 0.05 * ref for v in its.values()), its
+
+
 @pytest.mark.parametrize("tile", ["32x8", "40x8"])
 def test_fp64_tiles(rw, tile):
     c = P.random_case((21, 45, 50), seed=9, seed_frac=0.05, beta=40.0)
