@@ -817,10 +817,13 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
                              &R->sweeps, cap, &R->ms_sweeps));
         // residual replacement: x_hi absorbs the FP32 correction, the FP64
         // residual replaces the recursive one and the search direction is kept
+        // (only the systems that iterated in this round: the others' x did not change)
         if (!cur64) CK(counted(launch_accumulate(bx, ps.pad, P.code, delta, P.x_hi, w->stream)));
         ra.keep_p = 1;
+        ra.only_moved = 1;
         CK(counted(launch_residual(cur64, ra, delta, w->stream)));
-        CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream)));
+        CK(counted(launch_box_reduce(rpart, bpb, bx.nbox, sc, 0, w->stream, 1)));
+        ra.only_moved = 0;
         CK(cudaMemcpyAsync(h.data(), sc, bx.nbox * sizeof(BoxScalars), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaStreamSynchronize(w->stream));
         // FP32 sweeps failed a system when its round ended in a breakdown or

@@ -29,7 +29,7 @@ struct BoxScalars {
     int nfree;
     unsigned counter;  // arrival counter of the last-block reduction
     int status;      // 0 ok, 5 breakdown (restart next round)
-    int pad;
+    int moved;       // 1 when the box iterates in the current refinement round (its x changes)
 };
 
 // A batch of equally padded boxes: box b covers [0,nx) x [0,ny) x [0,nz) in
@@ -208,6 +208,7 @@ struct ResidArgs {
     // each, caller layout) from launch_weights64; null: computed in place
     const double* w3 = nullptr;
     int sqrt_g = 0;  // Poisson weights: the Gaussian form on sqrt(g) (mbeta is then -beta/2)
+    int only_moved = 0;  // 1: skip the boxes that did not iterate in the last round (their residual stands)
 };
 cudaError_t launch_init_x(int fp64, const ResidArgs& a, cudaStream_t s);
 // FP64 edge weights, each edge once (its lower voxel's forward edge), for the
@@ -217,8 +218,9 @@ cudaError_t launch_weights64(const ResidArgs& a, double* w3, cudaStream_t s);
 cudaError_t launch_residual(int fp64, const ResidArgs& a, float* delta, cudaStream_t s);
 cudaError_t launch_accumulate(const Boxes& bx, const Pad& pad, const uint8_t* code, const float* delta, double* x,
                               cudaStream_t s);
+// only_moved = 1: only the boxes that iterated in the last round (BoxScalars::moved)
 cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, BoxScalars* sc, int first,
-                              cudaStream_t s);
+                              cudaStream_t s, int only_moved = 0);
 cudaError_t launch_start_round(BoxScalars* sc, int nbox, int round, double tol, double eps_inner, int max_iter,
                                int restart, int* n_active, cudaStream_t s);
 cudaError_t launch_zero_homog(int fp64, const Boxes& bx, const uint8_t* code, const BoxScalars* sc, void* x,

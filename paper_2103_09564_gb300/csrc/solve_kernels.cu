@@ -148,6 +148,9 @@ __global__ void k_init_x(const ResidArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delta) {
     const int box = blockIdx.y;
+    // a box that did not iterate since its last residual keeps it (and its
+    // zero correction); k_box_reduce skips it the same way
+    if (a.only_moved && !a.sc[box].moved) return;
     const int nx = a.bx.nx, ny = a.bx.ny, nz = a.bx.nz;
     const int64_t nvox = (int64_t)nx * ny * nz;
     // up to 4 voxels per thread, a grid stride apart (blocks_per_box blocks
@@ -195,8 +198,7 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
                         const int64_t ntot = (int64_t)a.bx.nbox * nvox;
                         w = a.w3[(int64_t)(k >> 1) * ntot + ((k & 1) ? i : j)];
                     } else {
-                        const double dg = gi - gdbl_w(a, j);
-                        w = fmax(exp(a.mbeta * dg * dg), a.wmin);
+                        w = weight64(gi - gdbl_w(a, j), a.mbeta, a.wmin);
                     }
                     const double xj = xh[j];
                     d += (T)w;
@@ -241,8 +243,9 @@ __global__ void __launch_bounds__(256) k_residual(const ResidArgs a, float* delt
     }
 }
 
-// Forward FP64 weights of every voxel: the same expression, in the same
-// operand order up to an exact sign, as the residual's own evaluation.
+// Forward FP64 weights of every voxel: the same function (weight64), on the
+// same operands up to an exact sign, as the residual's own evaluation and the
+// FP64 sweeps'.
 __global__ void k_weights64(const ResidArgs a, double* w3) {
     const int box = blockIdx.y;
     const int nx = a.bx.nx, ny = a.bx.ny, nz = a.bx.nz;
@@ -264,8 +267,7 @@ __global__ void k_weights64(const ResidArgs a, double* w3) {
             if (!in[k]) continue;
             const int64_t j = i + st[k];
             if (a.code[j] == ABSENT) continue;
-            const double dg = gi - gdbl_w(a, j);
-            wv[k] = fmax(exp(a.mbeta * dg * dg), a.wmin);
+            wv[k] = weight64(gi - gdbl_w(a, j), a.mbeta, a.wmin);
         }
     }
 #pragma unroll
@@ -294,9 +296,10 @@ cudaError_t launch_residual(int fp64, const ResidArgs& a, float* delta, cudaStre
     return cudaGetLastError();
 }
 
-__global__ void k_box_reduce(const double* part, int bpb, BoxScalars* sc, int first) {
+__global__ void k_box_reduce(const double* part, int bpb, BoxScalars* sc, int first, int only_moved) {
     __shared__ double red[4][256];
     const int box = blockIdx.x;
+    if (only_moved && !sc[box].moved) return;
     double v[4] = {0, 0, 0, 0};
     for (int k = threadIdx.x; k < bpb; k += 256)
         for (int j = 0; j < 4; ++j) v[j] += part[((int64_t)box * bpb + k) * 4 + j];
@@ -319,8 +322,8 @@ __global__ void k_box_reduce(const double* part, int bpb, BoxScalars* sc, int fi
 }
 
 cudaError_t launch_box_reduce(const double* part, int blocks_per_box, int nbox, BoxScalars* sc, int first,
-                              cudaStream_t s) {
-    k_box_reduce<<<nbox, 256, 0, s>>>(part, blocks_per_box, sc, first);
+                              cudaStream_t s, int only_moved) {
+    k_box_reduce<<<nbox, 256, 0, s>>>(part, blocks_per_box, sc, first, only_moved);
     return cudaGetLastError();
 }
 
@@ -341,6 +344,7 @@ __global__ void k_start_round(BoxScalars* sc, int nbox, int round, double tol, d
     const double tgt = tol * tol * S->bb;
     const bool need = S->nseed > 0 && S->nfree > 0 && S->bb > 0.0 && S->rr_true > tgt && S->iters < max_iter;
     S->counter = 0u;
+    S->moved = need ? 1 : 0;
     // the residual that precedes every round wrote u (and the kept p) into
     // buffer 0: the record must point there, for the sweeps that read the
     // system's own parity (the cluster-resident solver)

@@ -42,6 +42,8 @@ __device__ __forceinline__ float ex2_approx(float a) {
     return r;
 }
 
+__device__ __forceinline__ double weight64(double dg, double mbeta, double wmin);  // below
+
 template <typename T>
 struct Num;
 template <>
@@ -56,8 +58,7 @@ template <>
 struct Num<double> {
     typedef double acc;
     __device__ __forceinline__ static double w(double a, double b, const SweepArgs& A) {
-        const double d = a - b;
-        return fmax(exp(A.mbeta * d * d), A.wmin);
+        return weight64(a - b, A.mbeta, A.wmin);
     }
 };
 
@@ -166,6 +167,40 @@ __device__ __forceinline__ DF df_of(double x) {
 __device__ __forceinline__ double df_dbl(DF a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ DF df_shfl_xor(DF a, int m) {
     return DF{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
+// exp(x) for x <= 0 in double-FP32: the argument reduced by k ln 2 (ln 2 as
+// a two-float constant, k = round(x log2 e)), a Taylor series of degree 12 on
+// |r| <= ln 2 / 2 in Horner form, scaled by 2^k.  Relative error below 5e-13
+// for x >= -69 (e^-69 ~ 1e-30, the default w_min; the two-float argument
+// carries |x| 2^-48 of absolute error); below that the low part underflows
+// (1e-8 relative at e^-87), and x < -87 gives 0 (the caller's floor applies).
+__host__ __device__ constexpr double df_inv_fact(int n) { return n <= 1 ? 1.0 : df_inv_fact(n - 1) / n; }
+#define RW_DF_CONST(v) DF{(float)(v), (float)((v) - (double)(float)(v))}
+__device__ __forceinline__ DF df_exp_neg(DF x) {
+    if (!(x.hi >= -87.0f)) return DF{0.0f, 0.0f};
+    constexpr double kLn2 = 0.69314718055994530942;
+    const float k = rintf(x.hi * 1.44269504088896341f);
+    const DF r = df_add(x, df_neg(df_mul(DF{k, 0.0f}, RW_DF_CONST(kLn2))));
+    DF p = RW_DF_CONST(df_inv_fact(12));
+#define RW_HORNER(n) p = df_add(df_mul(p, r), RW_DF_CONST(df_inv_fact(n)))
+    RW_HORNER(11); RW_HORNER(10); RW_HORNER(9); RW_HORNER(8); RW_HORNER(7); RW_HORNER(6);
+    RW_HORNER(5); RW_HORNER(4); RW_HORNER(3); RW_HORNER(2); RW_HORNER(1); RW_HORNER(0);
+#undef RW_HORNER
+    const float sc = __int_as_float((127 + (int)k) << 23);  // 2^k, k in [-126, 0]
+    return DF{p.hi * sc, p.lo * sc};
+}
+#undef RW_DF_CONST
+
+// The FP64 edge weight max(exp(mbeta dg^2), w_min) (mbeta = -beta) of the
+// residual and of the FP64 sweeps: the argument in FP64, the exponential in
+// double-FP32 on the FP32 pipes (GB300's FP64 rate makes an FP64 exp the
+// cost of a residual pass).
+__device__ __forceinline__ double weight64(double dg, double mbeta, double wmin) {
+    const double t = mbeta * dg * dg;
+    const float th = (float)t;
+    const DF e = df_exp_neg(DF{th, (float)(t - (double)th)});
+    return fmax((double)e.hi + (double)e.lo, wmin);
 }
 
 // finalize_box (below) in double-FP32: the same recurrences and decisions on
