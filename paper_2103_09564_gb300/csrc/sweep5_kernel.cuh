@@ -275,9 +275,16 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep5(const __grid_constant__ Swe
     // then the halo (strip 0 of every row; rows -1 and TY+1), then idle.
     const int tid = threadIdx.x;
     constexpr int NX = TX / V, NIN = TY * NX, NSN = TY + NX + 1, NHA = RY + 2 * (SX - 1);
+    // owning strips: the first 8k strips of every row first (a quarter warp of
+    // 128-bit shared loads then reads 128 contiguous bytes of one row), then
+    // the remaining NX - 8k strips of every row
+    constexpr int NX8 = NX / 8 * 8, NXR = NX - NX8 > 0 ? NX - NX8 : 1;  // (NXR unused when NX % 8 == 0)
     int sx, ry;
-    if (tid < NIN) {
-        ry = 1 + tid / NX, sx = 1 + tid % NX;
+    if (tid < TY * NX8) {
+        ry = 1 + tid / NX8, sx = 1 + tid % NX8;
+    } else if (tid < NIN) {
+        const int k = tid - TY * NX8;
+        ry = 1 + k / NXR, sx = 1 + NX8 + k % NXR;
     } else if (tid < NIN + NSN) {
         const int k = tid - NIN;
         if (k < TY) ry = 1 + k, sx = SX - 1;
