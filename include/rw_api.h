@@ -148,7 +148,7 @@ enum { RW_TILE_AUTO = 0,
        /* FP64 sweeps (RW_FP64 and the FP64 fallback); 32x8 is also the FP32
         * tile for boxes narrower than 25 voxels in x */
        RW_TILE_40x8 = 3, RW_TILE_32x8 = 7,
-       /* FP32 register-blocked strips of 4 voxels (padded layout, x margin 4):
+       /* FP32 register-blocked strips of 4 voxels:
         * 2 planes in flight, 3 (_D3) or 1 (_D1; s64x14_d1: 320 threads) */
        RW_TILE_S64x11 = 20, RW_TILE_S32x22 = 21, RW_TILE_S32x20 = 22, RW_TILE_S64x8 = 23,
        RW_TILE_S40x20 = 24, RW_TILE_S40x8 = 25,

@@ -30,7 +30,7 @@
 // CTA's table.  Every CTA then runs the same scalar recurrences on the same
 // sums in the same order, so all of them take the same exit.  A launch runs
 // up to `loop_iters` iterations of each system; the state is read from and
-// written back to the padded global arrays of the system's current buffer
+// written back to the global arrays (the strip kernel's layout) of the system's current buffer
 // parity (BoxScalars::par, unchanged), so the batched driver continues from
 // it (refinement rounds, FP64 residual).  Clusters never wait on each other:
 // each one takes systems of the list in turn.
@@ -135,7 +135,6 @@ __global__ void __launch_bounds__(kClNT, 1) k_brick_cluster(const __grid_constan
     const int RPI = kClNT / NX;
     const int tx = tid % NX, trow = tid / NX;
     const bool tlive = trow < RPI;
-    // padded layout: x margin 4, y and z margins 2, margins absent
     // the strip kernel's layout (no margins, rows of A.px >= NX voxels): system row R = z NY + y
     auto gidx = [&](int64_t gbase, int R) -> int64_t { return gbase + (int64_t)R * A.px + tx; };
 

@@ -174,9 +174,9 @@ std::map<std::string, Tuned> g_tuned;  // problem class -> autotuned sweep confi
 
 std::vector<int> tile_candidates(int fp64, int gtype, int nx) {
     // one list holds tiles of one layout family only (the autotuner times
-    // them on the same live vectors): the strip kernel's tiles (padded
-    // layout, x margin 4), or the unpadded k_sweep2 tile for boxes narrower
-    // than one padded tile
+    // them on the same live vectors): the strip kernel's tiles (its own
+    // layout, rows of a multiple of 4 voxels), or the caller-layout k_sweep2
+    // tile for boxes narrower than a strip tile
     std::vector<int> c;
     (void)gtype;
     if (fp64) {
@@ -261,10 +261,10 @@ std::string class_key(int fp64, int gtype, const Boxes& bx) {
 // The PCG driver.
 
 
-// TMA descriptors for a strip-sweep launch: the padded arrays as 3-D tensors
-// [PZ * nbox][PY][PX] of 4-byte words; boxes (TX + 2V) x (TY + 3) x 1 for u, p
-// and the g words, TX (V = 4) or TX + 2V (V = 2) x TY x 1 for delta.  `loop`
-// adds the maps of u_out / p_out, read by the odd iterations of a looped sweep.
+// TMA descriptors for a strip-sweep launch: the arrays as 4-D tensors
+// [nbox][PZ][PY][PX] of 4-byte words; boxes (TX + 2V) x (TY + 3) x 1 x 1 for u,
+// p and the g words, TX x TY x 1 x 1 for delta.  `loop` adds the maps of
+// u_out / p_out, read by the odd iterations of a looped sweep.
 rw_status strip_maps(int tile, SweepArgs* sa, bool loop = false) {
     if (tile < TILE_STRIP_FIRST) return RW_OK;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
@@ -288,8 +288,7 @@ rw_status strip_maps(int tile, SweepArgs* sa, bool loop = false) {
     const cuuint64_t gstr[3] = {(cuuint64_t)sa->px * 4, (cuuint64_t)sa->px * (cuuint64_t)sa->py * 4,
                                 (cuuint64_t)sa->px * (cuuint64_t)sa->py * (cuuint64_t)sa->pz * 4};
     const cuuint32_t box_t[4] = {(cuuint32_t)(tx + 2 * v), (cuuint32_t)(ty + 3), 1u, 1u};
-    // delta: the interior for 4-voxel strips, the full strip width for 2-voxel
-    // strips (whose interior does not start 16-byte aligned)
+    // delta: the tile's interior (its first column starts 16-byte aligned)
     const cuuint32_t box_x[4] = {(cuuint32_t)(v == 4 ? tx : tx + 2 * v), (cuuint32_t)ty, 1u, 1u};
     const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
     auto enc = [&](CUtensorMap* m, const void* ptr, const cuuint32_t* box, bool nan_fill = false) {
@@ -370,7 +369,7 @@ rw_status run_graph_chunks(DevWorkspace* w, const SweepCfg& cfg0, SweepArgs sa, 
     const int occ_loop = fp64 ? 0 : sweep5_occupancy_loop(cfg0.tile);
     bool loop = false;
     int lpar = 0;  // buffer parity of the next looped launch
-    // cluster-resident mode (FP32 sweeps in the strip kernels' padded layout,
+    // cluster-resident mode (FP32 sweeps in the strip kernels' layout,
     // small boxes): once the active systems are at most kClusterTurns per
     // resident cluster, the remaining iterations run there; each system keeps
     // its buffer parity
@@ -756,7 +755,7 @@ rw_status solve_boxes(DevWorkspace* w, const SolveProblem& P, const rw_opts& o, 
     uint32_t* gc = nullptr;
     if (!cur64) {
         RCK(ws_get_t(w, S_GC, ps.nvec * 4, &gc));
-        // the strip kernel's format marks absent voxels (margins included) NaN
+        // the strip kernel's format marks absent voxels (the columns beyond nx included) NaN
         const int fmt = ps.cands[0] >= TILE_STRIP_FIRST ? 1 : 0;
         if (fmt) CK(counted(launch_fill_u32(gc, ps.nvec, GC_ABSENT, w->stream)));
         else if (ps.pad.px) CK(cudaMemsetAsync(gc, 0, ps.nvec * 4, w->stream));

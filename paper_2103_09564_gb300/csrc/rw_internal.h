@@ -32,7 +32,7 @@ struct BoxScalars {
     int moved;       // 1 when the box iterates in the current refinement round (its x changes)
 };
 
-// A batch of equally padded boxes: box b covers [0,nx) x [0,ny) x [0,nz) in
+// A batch of equally sized boxes: box b covers [0,nx) x [0,ny) x [0,nz) in
 // its own storage; voxels at or beyond ext[b] are absent.
 struct Boxes {
     int nbox;
@@ -85,7 +85,7 @@ enum GType { G_U16 = 0, G_F32 = 1 };
 enum TileId {
     TILE_40x8 = 3,   // FP64 sweep (k_sweep)
     TILE_32x8 = 7,   // FP64 sweep, and the FP32 k_sweep2 for boxes narrower than a strip tile
-    // FP32 strip kernel (k_sweep5, strips of 4 voxels), padded layout
+    // FP32 strip kernel (k_sweep5, strips of 4 voxels), its own layout (Pad)
     TILE_S64x11 = 20, TILE_S32x22 = 21, TILE_S32x20 = 22, TILE_S64x8 = 23, TILE_S40x20 = 24, TILE_S40x8 = 25,
     TILE_S32x20_D3 = 31, TILE_S64x8_D3 = 32, TILE_S32x22_D1 = 33, TILE_S64x8_D1 = 34, TILE_S64x14_D1 = 35,
     // strips whose p_k and u' are exchanged through the TMA ring slots
@@ -95,14 +95,14 @@ enum TileId {
     TILE_R40x20_D2 = 44, TILE_R40x20_D3 = 45, TILE_R40x8_D2 = 46 };
 constexpr int N_TILES = 47;
 constexpr int TILE_RING_FIRST = TILE_R64x14_D2;  // k_sweep5 with the ring exchange
-constexpr int TILE_STRIP_FIRST = TILE_S64x11;    // tiles from here on: k_sweep5, padded layout
+constexpr int TILE_STRIP_FIRST = TILE_S64x11;    // tiles from here on: k_sweep5, the strip layout
 // Whether a tile id names a compiled sweep of this precision.
 inline bool tile_compiled(int fp64, int tile) {
     if (fp64) return tile == TILE_40x8 || tile == TILE_32x8;
     return tile == TILE_32x8 || (tile >= TILE_S64x11 && tile <= TILE_S40x8) ||
            (tile >= TILE_S32x20_D3 && tile < N_TILES);
 }
-// x margin of the padded layout: the strip width of k_sweep5
+// the strip width of k_sweep5 (4), else 2
 inline int tile_margin(int tile) { return tile >= TILE_STRIP_FIRST ? 4 : 2; }
 
 // Sweep launchers (sweep_*.cu).  Return cudaErrorInvalidValue for a
@@ -116,8 +116,8 @@ cudaError_t launch_sweep(int fp64, int gtype, int tile, const SweepArgs& a, int 
 // Cluster-resident PCG (cluster_kernel.cu): one thread-block cluster per
 // system, the system's FP32 state in the shared memory of its CTAs across the
 // iterations of a launch.  Systems of at most kClusterMaxDim voxels per axis
-// and at least as many z planes as CTAs per cluster, the strip kernels'
-// padded layout (x margin 4, y and z margins 2).
+// and at least as many z planes as CTAs per cluster, in the strip kernels'
+// layout.
 constexpr int kClusterMaxDim = 40;
 constexpr int kClusterSize = 16;
 // The cluster-resident solver takes over once the active systems are at most
